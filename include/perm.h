@@ -1,0 +1,285 @@
+/*
+ * perm.h -- C ABI of the GB300 sparse-permanent library (libperm.so).
+ *
+ * What it computes (Elbek & Kaya, "Fully-Automated Code Generation for
+ * Efficient Computation of Sparse Matrix Permanents on GPUs"):
+ *
+ *   perm(A) = sum over permutations s of prod_i a_{i,s(i)}                (Eq. 1)
+ *
+ * evaluated with the Nijenhuis-Wilf form of Ryser's formula (Eq. 2, Sec. II):
+ * the 2^(n-1) subsets of the first n-1 columns are walked in Gray-code order
+ * (Algorithm 1), each GPU thread owning an aligned chunk of the walk (Sec. II-A,
+ * Lemma 1) and keeping its row-sum vector x in registers (Sec. III), with the
+ * rows of x split between registers and global memory under the permanent
+ * ordering and partitioning of Sec. V (Algorithms 3 and 4).
+ *
+ * Conventions shared by every entry point:
+ *   - No C++ exception crosses this boundary.  Every call returns a
+ *     perm_status_t; perm_last_error() gives a thread-local message for the
+ *     last failing call on the calling thread.
+ *   - Matrices are borrowed for the duration of the call: the library copies
+ *     what it keeps (into plan- or server-owned host and device memory).
+ *     Result structs are caller-allocated.  Handles are opaque.
+ *   - Matrices are square, 1 <= n <= 64, given in CSR or CSC with 0-based
+ *     int32 indices strictly increasing inside each row (CSR) or column (CSC).
+ *     Out-of-range or repeated indices give PERM_ERR_PATTERN.  Explicit zero
+ *     values are dropped on ingest.
+ *   - Streams are cudaStream_t values passed as void*; NULL is the legacy
+ *     default stream.  A call that takes a stream returns after the result has
+ *     been copied back (it synchronises that stream).
+ *   - FP64 results carry the permanent as an unevaluated pair f64 + f64_lo.
+ *     Exact results (PERM_I64 inputs) are bit-exact; the plan refuses inputs
+ *     whose a-priori bound does not fit the widest exact mode (PERM_ERR_OVERFLOW).
+ *   - Every kernel the library launches is its own hand-written CUDA (or CUDA
+ *     C++ it generates and compiles with NVRTC for sm_103a).  There is no CPU
+ *     fallback: without a usable CUDA device the compute calls return
+ *     PERM_ERR_CUDA.
+ */
+#ifndef PERM_H
+#define PERM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PERM_OK = 0,
+    PERM_ERR_ARG = 1,        /* NULL pointer, bad enum, bad option value            */
+    PERM_ERR_SIZE = 2,       /* n outside [1, 64], nnz inconsistent, count < 0      */
+    PERM_ERR_PATTERN = 3,    /* index out of range / not strictly increasing        */
+    PERM_ERR_OVERFLOW = 4,   /* exact path: |perm| bound too large for 2^191 mode;  */
+                             /* or integer entries too large for int32 row sums     */
+    PERM_ERR_CUDA = 5,       /* a CUDA runtime/driver call failed (see last error)  */
+    PERM_ERR_NVRTC = 6,      /* generating/compiling a per-matrix kernel failed     */
+    PERM_ERR_NOMEM = 7,      /* host or device allocation failed                    */
+    PERM_ERR_TIMEOUT = 8,    /* a device-side wait ran out of iterations/time       */
+    PERM_ERR_BUSY = 9,       /* server refused a submit (admission budget full)     */
+    PERM_ERR_NOT_READY = 10, /* perm_poll: the ticket has not finished yet          */
+    PERM_ERR_CANCELLED = 11, /* server shut down before the ticket finished         */
+    PERM_ERR_INTERNAL = 12   /* a self-check failed (e.g. exact sum not divisible)  */
+} perm_status_t;
+
+/* The value type of a matrix selects the arithmetic path. */
+typedef enum {
+    PERM_F64 = 0,  /* double entries; FP64 walk, compensated reduction            */
+    PERM_I64 = 1   /* int64 entries; exact walk modulo 2^(64w), w = 1..3          */
+} perm_value_t;
+
+typedef enum { PERM_CSR = 0, PERM_CSC = 1 } perm_layout_t;
+
+/* A borrowed sparse matrix.  ptr has n+1 entries, idx and vals have nnz.
+   vals points to double (PERM_F64) or int64_t (PERM_I64). */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    perm_layout_t layout;
+    const int32_t *ptr;
+    const int32_t *idx;
+    perm_value_t vtype;
+    const void *vals;
+} perm_matrix_t;
+
+/* Column ordering (Sec. V and Sec. VI-B).  The last column of the order is the
+   one the Nijenhuis-Wilf variant never flips. */
+enum {
+    PERM_ORDER_AUTO = 0,    /* the cheaper of DEGREE and PAPER under the step-cost model */
+    PERM_ORDER_NONE = 1,    /* columns as given                                          */
+    PERM_ORDER_DEGREE = 2,  /* ascending nonzero count (Sec. VI-B, CPU-SparsePerman)    */
+    PERM_ORDER_PAPER = 3    /* PermanentOrdering, Algorithm 3                            */
+};
+
+/* Which kernel family runs the walk. */
+enum {
+    PERM_ENGINE_AUTO = 0,     /* codegen for single large matrices, generic otherwise     */
+    PERM_ENGINE_GENERIC = 1,  /* precompiled kernels, matrix read from shared memory      */
+    PERM_ENGINE_CODEGEN = 2   /* per-matrix CUDA C++ generated and compiled with NVRTC    */
+};
+
+/* Option flags. */
+enum {
+    PERM_FLAG_NO_KERNEL_CACHE = 1   /* codegen: compile even if this source was compiled before */
+};
+
+/* Options; a zeroed struct (or NULL) means "choose automatically". */
+typedef struct {
+    int32_t ordering;      /* PERM_ORDER_*                                                 */
+    int32_t engine;        /* PERM_ENGINE_*                                                */
+    int32_t reg_rows;      /* codegen: rows of x kept in registers (k of Algorithm 4);     */
+                           /*   0 = Algorithm 4 decides, n = all in registers              */
+    int32_t chunk_log2;    /* K: each thread walks aligned chunks of 2^K Gray indices;     */
+                           /*   0 = auto                                                   */
+    int32_t threads;       /* resident threads of the persistent grid; 0 = auto            */
+    int32_t exact_words;   /* exact path modulus 2^(64w): 0 = smallest w the bound allows  */
+    int32_t zero_skip;     /* 0 = on (skip 2^B-step blocks whose products are all zero),   */
+                           /*   1 = off                                                    */
+    int32_t flags;         /* PERM_FLAG_* bits                                             */
+    double gr_ratio;       /* Algorithm 4 GRratio; 0 = the library's GB300 value           */
+    uint64_t g_lo, g_hi;   /* Gray-index sub-range [g_lo, g_hi); both 0 = whole range.     */
+                           /*   Both ends must be multiples of 32.  A sub-range result is  */
+                           /*   the raw partial sum (see perm_result_t).                   */
+} perm_opts_t;
+
+/* Result of one permanent (or one Gray sub-range). */
+typedef struct {
+    perm_status_t status;
+    perm_value_t vtype;
+    /* PERM_F64: perm = f64 + f64_lo.  For a sub-range: the partial sum
+       sum_{g in [g_lo,g_hi)} (-1)^g prod_i x_i(g) (no final factor). */
+    double f64, f64_lo;
+    /* PERM_I64: perm as a signed 128-bit integer (lo word, hi word).      */
+    uint64_t i128_lo;
+    int64_t i128_hi;
+    /* PERM_I64 sub-range: sum_g (-1)^g prod_i 2x_i(g) modulo 2^(64 w),
+       little-endian words, w = exact_words.                              */
+    uint64_t partial[3];
+    int32_t exact_words;
+    int32_t engine;        /* PERM_ENGINE_GENERIC or PERM_ENGINE_CODEGEN that ran     */
+    int32_t ordering;      /* PERM_ORDER_* that was used                              */
+    int32_t reg_rows;      /* k: rows of x in registers                               */
+    int32_t reg_cols;      /* c: columns that touch register rows only               */
+    int32_t chunk_log2;    /* K                                                       */
+    int32_t threads;       /* resident threads of the launch                          */
+    int32_t regs_per_thread;
+    uint64_t steps;        /* Gray indices walked                                     */
+    double ms_plan;        /* host preprocessing                                      */
+    double ms_compile;     /* NVRTC + module load (0 when cached or generic)          */
+    double ms_kernel;      /* device time of the walk + reduction (CUDA events)       */
+    double fp_ops_per_step;/* counted arithmetic ops per Gray step (cost model)       */
+    double zero_skip_frac; /* fraction of 2^B-step blocks skipped as all-zero         */
+} perm_result_t;
+
+typedef struct perm_plan_s *perm_plan_t;
+
+/* Validates A, orders and partitions it (Algorithms 3 and 4), picks the chunk
+   plan, uploads what the kernels need and, for the codegen engine, generates
+   and compiles the matrix-specific kernel (cached by structure and values).
+   A matrix without a perfect matching (an empty row or column included) gets
+   a plan whose compute returns 0 without launching.  Needs a CUDA device.
+   Errors: ARG, SIZE, PATTERN, OVERFLOW, CUDA, NVRTC, NOMEM. */
+perm_status_t perm_plan_create(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_t *out);
+
+/* Runs the Gray-code walk of a plan on `stream` and fills *out.  The plan's
+   device buffers are reused; two perm_compute calls on one plan must not
+   overlap.  Errors: ARG, CUDA, INTERNAL. */
+perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out);
+
+/* Frees a plan (NULL is allowed). */
+void perm_plan_destroy(perm_plan_t plan);
+
+/* Computes `count` permanents in one persistent launch fed by a device work
+   queue (the matrices may differ in n and value type).  out has `count`
+   entries; out[i].status reports each matrix on its own.  opts applies to
+   every matrix (sub-ranges are not allowed here).
+   Errors: ARG, SIZE, CUDA, NOMEM (per-matrix PATTERN/OVERFLOW go to out[i]). */
+perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
+                         void *stream, perm_result_t *out);
+
+/* Same as perm_batch, but each matrix gets its own plan and its own launches
+   (the plain one-launch-per-matrix form, for comparison). */
+perm_status_t perm_batch_sequential(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
+                                    void *stream, perm_result_t *out);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct perm_server_s *perm_server_t;
+
+typedef struct {
+    int32_t max_inflight;     /* device slots (matrices resident at once); 0 = 4096          */
+    int32_t max_n;            /* largest n accepted; 0 = 40                                  */
+    double step_budget;       /* admission: Gray steps in flight at most; 0 = auto          */
+    int32_t device;           /* CUDA device ordinal                                        */
+    int32_t timeout_ms;       /* a request unfinished after this long fails with TIMEOUT;  */
+                              /*   0 = none                                                 */
+} perm_server_opts_t;
+
+/* Starts a serving loop: a host thread that admits submitted matrices into
+   device slots while earlier ones are still running, launches them in waves
+   on its own stream, and publishes results for perm_poll. */
+perm_status_t perm_server_create(const perm_server_opts_t *opts, perm_server_t *out);
+
+/* Queues one matrix (copied).  Returns BUSY when the admission budget is full
+   (the caller retries), SIZE for n > max_n.  *ticket identifies the request. */
+perm_status_t perm_submit(perm_server_t s, const perm_matrix_t *A, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0 = just check, <0 = forever) for a ticket.  Returns
+   OK with *out filled (out->status is the request's own status), NOT_READY,
+   or ARG for an unknown ticket.  A ticket can be collected once. */
+perm_status_t perm_poll(perm_server_t s, uint64_t ticket, int32_t timeout_ms, perm_result_t *out);
+
+/* Server-side latency statistics in milliseconds (submit -> result ready). */
+typedef struct {
+    uint64_t completed, rejected, failed;
+    double p50_ms, p99_ms, max_ms;
+    double perms_per_s;
+} perm_server_stats_t;
+
+perm_status_t perm_server_stats(perm_server_t s, perm_server_stats_t *out);
+
+/* Stops the loop, cancels unfinished tickets, frees everything (NULL is allowed). */
+void perm_server_destroy(perm_server_t s);
+
+/* ------------------------------------------------------------ inspection */
+/* Host-only calls (no GPU needed): they expose the preprocessing so that it
+   can be checked against the paper. */
+
+typedef struct {
+    int32_t n;
+    int32_t structurally_zero;   /* 1 if there is no perfect matching                */
+    int32_t ordering;            /* PERM_ORDER_* actually used                        */
+    int32_t col_order[64];       /* col_order[p] = original column at position p     */
+    int32_t row_order[64];       /* row_order[r] = original row at register slot r   */
+    int32_t group_of_row[64];    /* by slot: first ordered column touching the row   */
+    int32_t group_size[64];      /* |R_j|: rows whose first touching column is j     */
+    int32_t col_nnz[64];         /* nonzeros of ordered column j                     */
+    int32_t reg_rows, reg_cols;  /* k and c of Algorithm 4                           */
+    int32_t exact_words;         /* w for the exact path (0 for FP64 inputs)         */
+    double bound_log2;           /* log2 of the a-priori |perm| bound                */
+    double ops_per_step;         /* cost model: arithmetic ops per step, this scheme */
+    double ops_per_step_paper;   /* the same walk with a full product per step       */
+} perm_inspect_t;
+
+perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts, perm_inspect_t *out);
+
+/* Signed changed-bit sequence SCBS(k) of a k-bit Gray code (Sec. IV): the
+   2^k - 1 entries written to out as +(j+1) for inclusion of column j and
+   -(j+1) for exclusion, computed by Theorem 1 (j = ctz(i); sign + iff
+   floor(i / 2^(j+1)) is even).  k in [1, 24]. */
+perm_status_t perm_scbs(int32_t k, int32_t *out);
+
+/* GenerateLaunchParameters, Algorithm 2: for tau threads and dimension n,
+   writes up to max_launches triples (start, delta, end) and their count. */
+perm_status_t perm_alg2_launches(int64_t tau, int32_t n, int64_t *start, int64_t *delta, int64_t *end,
+                                 int32_t max_launches, int32_t *count);
+
+/* The CUDA C++ source that the codegen engine would compile for A (for
+   inspection).  Writes at most cap bytes including the terminating NUL and
+   sets *len to the full length. */
+perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opts, char *buf, int64_t cap,
+                                  int64_t *len);
+
+/* Measures this GPU's FP64 (DFMA) and 32-bit IMAD issue rates in lane
+   operations per second with two short probe kernels on `stream` (8
+   independent chains per thread, 8 blocks of 256 threads per SM).  These are
+   the ALU roofline denominators of the FP64 and exact walks. */
+perm_status_t perm_issue_rates(void *stream, double *fp64_ops_per_s, double *imad_ops_per_s);
+
+/* ------------------------------------------------------------- misc */
+
+const char *perm_status_string(perm_status_t s);
+const char *perm_last_error(void);
+/* 1 when a CUDA device is usable from this library, else 0 (never fails). */
+int32_t perm_device_available(void);
+/* Library version, e.g. "1.0.0". */
+const char *perm_version(void);
+/* sizeof of the ABI structs, so bindings can check their layout:
+   0 perm_matrix_t, 1 perm_opts_t, 2 perm_result_t, 3 perm_inspect_t,
+   4 perm_server_opts_t, 5 perm_server_stats_t; -1 for anything else. */
+int64_t perm_sizeof(int32_t which);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERM_H */

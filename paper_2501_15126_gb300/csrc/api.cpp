@@ -1,0 +1,558 @@
+// api.cpp -- the C ABI of libperm (see include/perm.h): plans, compute,
+// inspection helpers.  Batch and serving live in batch.cpp / server.cpp.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "codegen.hpp"
+#include "host.hpp"
+#include "kernels.hpp"
+#include "plan.hpp"
+
+namespace perm {
+
+static thread_local std::string g_last_error;
+
+perm_status_t fail(perm_status_t s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+perm_status_t cuda_fail(cudaError_t e, const char *what) {
+    return fail(PERM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int nmax_bucket(int n) {
+    if (n <= 16) return 16;
+    if (n <= 32) return 32;
+    if (n <= 48) return 48;
+    return 0;
+}
+
+static int floor_log2(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
+
+// Builds the shared-memory image read by the generic kernels.
+void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img) {
+    const int n = m.n;
+    const int last = L.col_order[n - 1];
+    const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
+    const size_t head = 16 + 8 * (size_t)nmax * 2;
+    img.assign(head + vsz * (size_t)nmax * (1 + (size_t)nmax), 0);
+    int32_t *hdr = reinterpret_cast<int32_t *>(img.data());
+    hdr[0] = n;
+    hdr[1] = L.top;
+    uint64_t *colmask = reinterpret_cast<uint64_t *>(img.data() + 16);
+    uint64_t *grpmask = colmask + nmax;
+    for (int p = 0; p + 1 < n; ++p) colmask[p] = L.colmask[p];
+    for (int g = 0; g < n; ++g)
+        for (int s = L.group_begin[g]; s < L.group_begin[g + 1]; ++s) grpmask[g] |= 1ull << s;
+    unsigned char *x0 = img.data() + head;
+    unsigned char *val = x0 + vsz * nmax;
+    for (int s = 0; s < n; ++s) {
+        const int r = L.row_order[s];
+        if (arith == 0) {
+            double rowsum = 0.0;
+            for (int j = 0; j < n; ++j) rowsum += m.fval(r, j);
+            const double v = m.fval(r, last) - rowsum / 2.0;
+            std::memcpy(x0 + vsz * s, &v, vsz);
+        } else {
+            int64_t rowsum = 0;
+            for (int j = 0; j < n; ++j) rowsum += m.ival(r, j);
+            const int v = (int)(2 * m.ival(r, last) - rowsum);
+            std::memcpy(x0 + vsz * s, &v, vsz);
+        }
+    }
+    for (int p = 0; p + 1 < n; ++p) {
+        const int c = L.col_order[p];
+        for (int s = 0; s < n; ++s) {
+            const int r = L.row_order[s];
+            if (!m.nz(r, c)) continue;
+            unsigned char *dst = val + vsz * ((size_t)p * nmax + s);
+            if (arith == 0) { const double v = m.fval(r, c); std::memcpy(dst, &v, vsz); }
+            else { const int v = (int)(2 * m.ival(r, c)); std::memcpy(dst, &v, vsz); }
+        }
+    }
+}
+
+// Checks that the exact walk's doubled row sums fit int32.
+static bool exact_fits_int32(const Matrix &m) {
+    for (int i = 0; i < m.n; ++i) {
+        int64_t s = 0;
+        for (int j = 0; j < m.n; ++j) {
+            const int64_t v = m.ival(i, j);
+            if (v > (1ll << 29) || v < -(1ll << 29)) return false;
+            s += v < 0 ? -v : v;
+            if (s > (1ll << 29)) return false;
+        }
+    }
+    return true;
+}
+
+perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, perm_plan_s &P) {
+    const double t0 = now_ms();
+    perm_opts_t opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    std::string err;
+    perm_status_t st = ingest(A, P.m, err);
+    if (st != PERM_OK) return fail(st, err);
+    const int n = P.m.n;
+    P.opts = opts;
+    P.arith = 0;
+    P.total = 1ull << (n - 1);
+    P.g_lo = opts.g_lo;
+    P.g_hi = opts.g_hi;
+    P.subrange = !(opts.g_lo == 0 && opts.g_hi == 0);
+    if (!P.subrange) { P.g_lo = 0; P.g_hi = P.total; }
+    if (P.g_lo > P.g_hi || P.g_hi > P.total) return fail(PERM_ERR_ARG, "sub-range outside [0, 2^(n-1))");
+    if (P.subrange && ((P.g_lo % 32) || ((P.g_hi % 32) && P.g_hi != P.total)))
+        return fail(PERM_ERR_ARG, "sub-range ends must be multiples of 32");
+    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_PAPER) return fail(PERM_ERR_ARG, "bad ordering");
+    if (opts.engine < 0 || opts.engine > PERM_ENGINE_CODEGEN) return fail(PERM_ERR_ARG, "bad engine");
+    if (opts.exact_words < 0 || opts.exact_words > 3) return fail(PERM_ERR_ARG, "exact_words must be 0..3");
+    if (opts.chunk_log2 < 0 || opts.chunk_log2 > 63) return fail(PERM_ERR_ARG, "bad chunk_log2");
+    if (opts.threads < 0) return fail(PERM_ERR_ARG, "threads < 0");
+    P.zero = !has_perfect_matching(P.m);
+    P.L = choose_layout(P.m, opts.ordering);
+    P.ops_per_step = cost_per_step(P.L, false);
+    P.ops_per_step_paper = cost_per_step(P.L, true);
+    if (P.m.is_int) {
+        const double b = bound_log2(P.m);
+        P.bound = b;
+        int w = exact_words_for(b, n);
+        if (!exact_fits_int32(P.m)) return fail(PERM_ERR_OVERFLOW, "integer entries too large for the exact walk");
+        if (!P.zero) {
+            if (opts.exact_words) {
+                if (!P.subrange && w && opts.exact_words < w)
+                    return fail(PERM_ERR_OVERFLOW, "exact_words too small for this matrix's bound");
+                w = opts.exact_words;
+            } else if (!w) {
+                if (P.subrange) w = 3;
+                else return fail(PERM_ERR_OVERFLOW, "|perm| bound exceeds the 2^191 exact mode");
+            }
+        }
+        P.arith = w ? w : 1;
+    }
+    P.ms_plan = now_ms() - t0;
+    return PERM_OK;
+}
+
+// Chooses K, grid and block for a walk over [g_lo, g_hi).
+static perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block) {
+    const uint64_t len = P.g_hi - P.g_lo;
+    const int n = P.m.n;
+    int kmax = n - 1;
+    if (P.g_lo) kmax = std::min(kmax, __builtin_ctzll(P.g_lo));
+    if (P.g_hi != P.total || P.subrange) kmax = std::min(kmax, P.g_hi ? __builtin_ctzll(P.g_hi) : 63);
+    kmax = std::min(kmax, floor_log2(len));
+    const int64_t resident_warps = (int64_t)kSMCount * blocks_per_sm * (block / 32);
+    int K = P.opts.chunk_log2;
+    if (!K) {
+        // enough 32-chunk tasks for every resident warp several times over
+        const double want_tasks = 8.0 * (double)resident_warps;
+        K = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * want_tasks)));
+        K = std::max(K, block_log2 + 8);   // amortise the start vector over >= 2^(B+8) steps
+    }
+    K = std::min(K, kmax);
+    if (K < block_log2) return fail(PERM_ERR_ARG, "range too short or misaligned for the chunk size");
+    P.K = K;
+    P.chunk_lo = P.g_lo >> K;
+    P.chunk_hi = P.g_hi >> K;
+    P.ntasks = (P.chunk_hi - P.chunk_lo + 31) / 32;
+    P.block = block;
+    int64_t grid = (int64_t)kSMCount * blocks_per_sm;
+    if (P.opts.threads) grid = std::max<int64_t>(1, P.opts.threads / block);
+    grid = std::min<int64_t>(grid, ((int64_t)P.ntasks * 32 + block - 1) / block);
+    P.grid = (int)std::max<int64_t>(1, grid);
+    return PERM_OK;
+}
+
+// The register rows requested by the caller, rounded down to whole groups.
+void split_for_rows(const Layout &L, int rows, int *k, int *c) {
+    const int n = L.n;
+    rows = std::min(rows, n);
+    int cc = 0;
+    while (cc + 1 <= n - 1 && L.group_begin[cc + 1] <= rows) ++cc;
+    *c = cc;
+    *k = L.group_begin[cc];
+}
+
+// The generated kernel keeps every row reached inside the unrolled block in
+// registers: c >= B.  k = n means no global rows.
+void normalise_split(const Layout &L, int *k, int *c) {
+    const int n = L.n;
+    const int B = CodegenKernel().block_log2;
+    if (*c < B) { *c = std::min(B, n - 1); *k = L.group_begin[*c]; }
+    if (*c >= n - 1 || *k >= n) { *k = n; *c = n - 1; }
+    if (*k < 1) *k = 1;
+}
+
+perm_status_t plan_device_setup(perm_plan_s &P) {
+    const int n = P.m.n;
+    cudaError_t e;
+    const double t0 = now_ms();
+    if (P.zero) return PERM_OK;
+    int engine = P.opts.engine;
+    const bool tiny = n <= 8;
+    if (engine == PERM_ENGINE_AUTO) engine = (n > 48 || (!tiny && P.len() >= (1ull << 30))) ? PERM_ENGINE_CODEGEN
+                                                                                            : PERM_ENGINE_GENERIC;
+    if (engine == PERM_ENGINE_GENERIC && n > 48) return fail(PERM_ERR_SIZE, "generic kernels cover n <= 48");
+    const int nmax = nmax_bucket(std::min(n, 48));
+    if (tiny) engine = PERM_ENGINE_GENERIC;
+    P.engine = engine;
+    P.words = P.arith == 0 ? 2 : P.arith;
+
+    if (engine == PERM_ENGINE_GENERIC) {
+        P.gf = generic_fns(nmax, P.arith);
+        if (!P.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this size");
+        P.nmax = nmax;
+        std::vector<unsigned char> img;
+        build_devmat(P.m, P.L, P.arith, nmax, img);
+        if ((e = cudaMalloc(&P.d_devmat, img.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(devmat)");
+        if ((e = cudaMemcpy(P.d_devmat, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(devmat)");
+        cudaFuncAttributes attr;
+        if ((e = P.gf.attr(&attr)) != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        P.regs = attr.numRegs;
+        if (tiny) {
+            P.direct = true;
+            P.block = 256;
+            P.grid = (int)((P.g_hi - P.g_lo + 255) / 256);
+            P.ntasks = (uint64_t)P.grid;
+            P.K = 0;
+        } else {
+            int bps = 0;
+            if ((e = P.gf.occ(256, &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
+            perm_status_t st = choose_launch(P, P.gf.block_log2, std::max(bps, 1), 256);
+            if (st != PERM_OK) return st;
+        }
+    } else {
+        int k = n, c = n - 1;
+        const double gr = P.opts.gr_ratio > 0 ? P.opts.gr_ratio : kDefaultGRRatio;
+        partition_alg4(P.L, gr, kCodegenBaseRegs, &k, &c);   // Algorithm 4
+        if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
+        normalise_split(P.L, &k, &c);
+        P.k = k;
+        P.c = c;
+        std::string err;
+        perm_status_t st = codegen_build(P, err);
+        if (st != PERM_OK) return fail(st, err);
+        st = choose_launch(P, P.cg.block_log2, std::max(P.cg.blocks_per_sm, 1), P.cg.block);
+        if (st != PERM_OK) return st;
+        if (P.k < n) {
+            const size_t bytes = (size_t)(n - P.k) * (size_t)P.grid * P.block * (P.arith == 0 ? 8 : 4);
+            if ((e = cudaMalloc(&P.d_xglob, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(x global rows)");
+        }
+    }
+    const size_t ws_words = kWsTaskOut + (size_t)P.ntasks * P.words;
+    if ((e = cudaMalloc(&P.d_ws, ws_words * 8)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    if (engine == PERM_ENGINE_GENERIC && !P.direct) {
+        pk::BatchMat bm;
+        std::memset(&bm, 0, sizeof(bm));
+        bm.task_begin = 0;
+        bm.chunk_lo = P.chunk_lo;
+        bm.chunk_hi = P.chunk_hi;
+        bm.K = P.K;
+        if ((e = cudaMemcpy(P.d_ws + kWsBatchMat, &bm, sizeof(bm), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(batch table)");
+    }
+    if ((e = cudaMallocHost(&P.h_res, 8 * 8)) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaEventCreate(&P.ev0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&P.ev1)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    P.ms_plan += now_ms() - t0 - P.ms_compile;
+    return PERM_OK;
+}
+
+// Launches the walk and the reduction; no synchronisation.
+perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(P.d_ws, 0, 8 * 8, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    uint64_t *task_out = P.d_ws + kWsTaskOut;
+    if ((e = cudaEventRecord(P.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if (P.direct) {
+        e = P.gf.direct(P.d_devmat, P.g_lo, P.g_hi, task_out, P.grid, P.block, st);
+        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+    } else if (P.engine == PERM_ENGINE_GENERIC) {
+        pk::BatchArgs ba;
+        ba.mats = reinterpret_cast<const pk::BatchMat *>(P.d_ws + kWsBatchMat);
+        ba.devmats = P.d_devmat;
+        ba.ntasks = P.ntasks;
+        ba.task_counter = reinterpret_cast<unsigned long long *>(P.d_ws);
+        ba.task_out = reinterpret_cast<unsigned long long *>(task_out);
+        ba.skip_counter = reinterpret_cast<unsigned long long *>(P.d_ws + 1);
+        ba.devmat_stride = P.gf.devmat_bytes;
+        ba.nmat = 1;
+        ba.zero_skip = P.opts.zero_skip ? 0 : 1;
+        e = P.gf.walk(ba, P.grid, P.block, st);
+        if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    } else {
+        pk::WalkArgs wa;
+        wa.chunk_lo = P.chunk_lo;
+        wa.chunk_hi = P.chunk_hi;
+        wa.ntasks = P.ntasks;
+        wa.task_counter = reinterpret_cast<unsigned long long *>(P.d_ws);
+        wa.task_out = reinterpret_cast<unsigned long long *>(task_out);
+        wa.skip_counter = reinterpret_cast<unsigned long long *>(P.d_ws + 1);
+        wa.K = P.K;
+        wa.zero_skip = P.opts.zero_skip ? 0 : 1;
+        e = codegen_launch(P, wa, st);
+        if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    }
+    if ((e = reduce_launch(P.arith, task_out, P.ntasks, P.d_ws + 2, st)) != cudaSuccess)
+        return cuda_fail(e, "reduce kernel launch");
+    if ((e = cudaEventRecord(P.ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if ((e = cudaMemcpyAsync(P.h_res, P.d_ws, 8 * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(result)");
+    return PERM_OK;
+}
+
+// Fills the descriptive fields of a result from a prepared plan.
+void describe(const perm_plan_s &P, perm_result_t *out) {
+    std::memset(out, 0, sizeof(*out));
+    const int n = P.m.n;
+    out->vtype = P.m.is_int ? PERM_I64 : PERM_F64;
+    out->engine = P.engine;
+    out->ordering = P.L.ordering;
+    out->reg_rows = P.engine == PERM_ENGINE_CODEGEN ? P.k : n;
+    out->reg_cols = P.engine == PERM_ENGINE_CODEGEN ? P.c : n - 1;
+    out->chunk_log2 = P.K;
+    out->threads = P.grid * P.block;
+    out->regs_per_thread = P.regs;
+    out->steps = P.zero ? 0 : P.g_hi - P.g_lo;
+    out->ms_plan = P.ms_plan;
+    out->ms_compile = P.ms_compile;
+    out->fp_ops_per_step = P.ops_per_step;
+    out->exact_words = P.m.is_int ? P.arith : 0;
+}
+
+// Turns a reduced raw sum (2 words FP64 hi/lo, or w exact words) into the
+// permanent (or the sub-range partial sum).
+perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *r, perm_result_t *out) {
+    const int n = P.m.n;
+    if (P.zero) { out->status = PERM_OK; return PERM_OK; }
+    if (!P.m.is_int) {
+        double hi, lo;
+        std::memcpy(&hi, &r[0], 8);
+        std::memcpy(&lo, &r[1], 8);
+        if (P.subrange) { out->f64 = hi; out->f64_lo = lo; }
+        else {
+            const double f = (n % 2) ? 2.0 : -2.0;    // 4 (n mod 2) - 2, Algorithm 1
+            out->f64 = hi * f;
+            out->f64_lo = lo * f;
+        }
+        out->status = PERM_OK;
+        return PERM_OK;
+    }
+    const int W = P.arith;
+    for (int i = 0; i < W; ++i) out->partial[i] = r[i];
+    if (P.subrange) { out->status = PERM_OK; return PERM_OK; }
+    // S = (-1)^(n-1) 2^(n-1) perm  (mod 2^(64W)): the low n-1 bits must vanish
+    const unsigned __int128 lo128 = ((unsigned __int128)(W >= 2 ? r[1] : 0) << 64) | r[0];
+    const uint64_t top = W >= 3 ? r[2] : 0;
+    const int shift = n - 1;
+    if (shift && (r[0] & ((shift >= 64) ? ~0ull : ((1ull << shift) - 1)))) {
+        out->status = PERM_ERR_INTERNAL;
+        return fail(PERM_ERR_INTERNAL, "exact sum not divisible by 2^(n-1)");
+    }
+    // value = S >> (n-1) as a (64W - n + 1)-bit two's complement number
+    unsigned __int128 v;
+    if (W == 3) v = (shift ? (lo128 >> shift) | ((unsigned __int128)top << (128 - shift)) : lo128);
+    else v = lo128 >> shift;
+    const int bits = 64 * W - shift;
+    if (bits < 128) {
+        const unsigned __int128 one = 1;
+        const unsigned __int128 mask = (one << bits) - 1;
+        v &= mask;
+        if ((v >> (bits - 1)) & 1) v |= ~mask;   // sign-extend
+    }
+    if ((n - 1) % 2) v = (unsigned __int128)0 - v;   // times (-1)^(n-1)
+    out->i128_lo = (uint64_t)v;
+    out->i128_hi = (int64_t)(uint64_t)(v >> 64);
+    out->status = PERM_OK;
+    return PERM_OK;
+}
+
+perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out) {
+    describe(P, out);
+    if (P.zero) { out->status = PERM_OK; return PERM_OK; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.ev0, P.ev1);
+    out->ms_kernel = ms;
+    const uint64_t skipped = P.h_res[1];
+    const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
+    const uint64_t blocks = (P.g_hi - P.g_lo) >> std::max(1, B);
+    out->zero_skip_frac = (!P.direct && blocks) ? (double)skipped / (double)blocks : 0.0;
+    return finish_raw(P, P.h_res + 2, out);
+}
+
+}  // namespace perm
+
+perm_plan_s::~perm_plan_s() {
+    if (d_devmat) cudaFree(d_devmat);
+    if (d_ws) cudaFree(d_ws);
+    if (d_xglob) cudaFree(d_xglob);
+    if (h_res) cudaFreeHost(h_res);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    perm::codegen_release(*this);
+}
+
+using namespace perm;
+
+extern "C" {
+
+perm_status_t perm_plan_create(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_t *out) {
+    if (!out) return fail(PERM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    perm_plan_s *P = new (std::nothrow) perm_plan_s();
+    if (!P) return fail(PERM_ERR_NOMEM, "out of host memory");
+    perm_status_t st = plan_prepare(A, opts, *P);
+    if (st == PERM_OK) st = plan_device_setup(*P);
+    if (st != PERM_OK) { delete P; return st; }
+    *out = P;
+    return PERM_OK;
+}
+
+perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out) {
+    if (!plan || !out) return fail(PERM_ERR_ARG, "NULL plan or result");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!plan->zero) {
+        perm_status_t s = plan_launch(*plan, st);
+        if (s != PERM_OK) { std::memset(out, 0, sizeof(*out)); out->status = s; return s; }
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { out->status = PERM_ERR_CUDA; return cuda_fail(e, "cudaStreamSynchronize"); }
+    }
+    return plan_finish(*plan, out);
+}
+
+void perm_plan_destroy(perm_plan_t plan) { delete plan; }
+
+perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, perm_inspect_t *out) {
+    if (!out) return fail(PERM_ERR_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    perm_opts_t opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    Matrix m;
+    std::string err;
+    perm_status_t st = ingest(A, m, err);
+    if (st != PERM_OK) return fail(st, err);
+    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_PAPER) return fail(PERM_ERR_ARG, "bad ordering");
+    const Layout L = choose_layout(m, opts.ordering);
+    out->n = m.n;
+    out->structurally_zero = has_perfect_matching(m) ? 0 : 1;
+    out->ordering = L.ordering;
+    for (int i = 0; i < m.n; ++i) {
+        out->col_order[i] = L.col_order[i];
+        out->row_order[i] = L.row_order[i];
+        out->group_of_row[i] = L.group_of_slot[i];
+        out->group_size[i] = L.group_begin[i + 1] - L.group_begin[i];
+        out->col_nnz[i] = L.col_nnz[i];
+    }
+    int k = m.n, c = m.n - 1;
+    partition_alg4(L, opts.gr_ratio > 0 ? opts.gr_ratio : kDefaultGRRatio, kCodegenBaseRegs, &k, &c);
+    out->reg_rows = k;
+    out->reg_cols = c;
+    out->bound_log2 = bound_log2(m);
+    out->exact_words = m.is_int ? exact_words_for(out->bound_log2, m.n) : 0;
+    out->ops_per_step = cost_per_step(L, false);
+    out->ops_per_step_paper = cost_per_step(L, true);
+    return PERM_OK;
+}
+
+perm_status_t perm_scbs(int32_t k, int32_t *out) {
+    if (!out || k < 1 || k > 24) return fail(PERM_ERR_ARG, "k must be in [1, 24]");
+    const uint64_t len = (1ull << k) - 1;
+    for (uint64_t i = 1; i <= len; ++i) out[i - 1] = scbs_sign(i) * (scbs_col(i) + 1);
+    return PERM_OK;
+}
+
+perm_status_t perm_alg2_launches(int64_t tau, int32_t n, int64_t *start, int64_t *delta, int64_t *end,
+                                 int32_t max_launches, int32_t *count) {
+    if (tau < 1 || n < 2 || n > 62 || !count) return fail(PERM_ERR_ARG, "bad Algorithm 2 arguments");
+    std::vector<Launch> v = alg2_launches(tau, n);
+    *count = (int32_t)v.size();
+    for (int i = 0; i < (int)v.size() && i < max_launches; ++i) {
+        if (start) start[i] = v[i].start;
+        if (delta) delta[i] = v[i].delta;
+        if (end) end[i] = v[i].end;
+    }
+    return PERM_OK;
+}
+
+perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opts, char *buf, int64_t cap,
+                                  int64_t *len) {
+    perm_plan_s P;
+    perm_status_t st = plan_prepare(A, opts, P);
+    if (st != PERM_OK) return st;
+    const int n = P.m.n;
+    int k = n, c = n - 1;
+    partition_alg4(P.L, (opts && opts->gr_ratio > 0) ? opts->gr_ratio : kDefaultGRRatio, kCodegenBaseRegs, &k, &c);
+    if (opts && opts->reg_rows > 0) split_for_rows(P.L, opts->reg_rows, &k, &c);
+    normalise_split(P.L, &k, &c);
+    P.k = k;
+    P.c = c;
+    std::string src = codegen_source(P);
+    if (len) *len = (int64_t)src.size();
+    if (buf && cap > 0) {
+        const size_t nb = std::min<size_t>((size_t)cap - 1, src.size());
+        std::memcpy(buf, src.data(), nb);
+        buf[nb] = 0;
+    }
+    return PERM_OK;
+}
+
+const char *perm_status_string(perm_status_t s) {
+    switch (s) {
+    case PERM_OK: return "ok";
+    case PERM_ERR_ARG: return "invalid argument";
+    case PERM_ERR_SIZE: return "invalid size";
+    case PERM_ERR_PATTERN: return "invalid sparsity pattern";
+    case PERM_ERR_OVERFLOW: return "exact result may overflow";
+    case PERM_ERR_CUDA: return "CUDA error";
+    case PERM_ERR_NVRTC: return "kernel generation/compilation failed";
+    case PERM_ERR_NOMEM: return "out of memory";
+    case PERM_ERR_TIMEOUT: return "timed out";
+    case PERM_ERR_BUSY: return "busy";
+    case PERM_ERR_NOT_READY: return "not ready";
+    case PERM_ERR_CANCELLED: return "cancelled";
+    case PERM_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *perm_last_error(void) { return g_last_error.c_str(); }
+
+int32_t perm_device_available(void) {
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) { cudaGetLastError(); return 0; }
+    return count > 0 ? 1 : 0;
+}
+
+const char *perm_version(void) { return "1.0.0"; }
+
+int64_t perm_sizeof(int32_t which) {
+    switch (which) {
+    case 0: return (int64_t)sizeof(perm_matrix_t);
+    case 1: return (int64_t)sizeof(perm_opts_t);
+    case 2: return (int64_t)sizeof(perm_result_t);
+    case 3: return (int64_t)sizeof(perm_inspect_t);
+    case 4: return (int64_t)sizeof(perm_server_opts_t);
+    case 5: return (int64_t)sizeof(perm_server_stats_t);
+    default: return -1;
+    }
+}
+
+}  // extern "C"

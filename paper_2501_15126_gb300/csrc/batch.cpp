@@ -1,0 +1,250 @@
+// batch.cpp -- many permanents in one persistent launch per kernel family.
+//
+// perm_batch: every matrix is prepared on the host (ingest, structural guard,
+// ordering, exact width); matrices are grouped by (NMAX bucket, arithmetic);
+// each group becomes one launch of the generic multi-matrix walk, fed by one
+// device task table (32-chunk tasks of every matrix of the group), followed by
+// one segmented reduction (one warp per matrix).  The chunk length of each
+// group comes from the autotuner (tune.cpp) unless the caller fixes it.
+// Tiny (n <= 8) and large (n > 48) matrices take their own plans.
+//
+// perm_batch_sequential: the plain form -- plan, launch, synchronise and
+// destroy one matrix at a time -- used as the comparison baseline.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "batch.hpp"
+#include "plan.hpp"
+
+namespace perm {
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+int batch_chunk_log2(int n, int B, int K_target) {
+    // 32 chunks fill a warp task; keep at least one full task when n allows
+    int K = std::min(K_target, n - 1 - 5);
+    K = std::max(K, B);
+    return std::min(K, n - 1);
+}
+
+int BatchGroup::setup(int nmax_, int arith_, int K_target) {
+    nmax = nmax_;
+    arith = arith_;
+    gf = generic_fns(nmax, arith);
+    if (!gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this group");
+    words = arith == 0 ? 2 : arith;
+    // task table
+    mats.resize(plans.size());
+    ntasks = 0;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        perm_plan_s &P = *plans[i];
+        const int K = batch_chunk_log2(P.m.n, gf.block_log2, K_target);
+        P.K = K;
+        P.chunk_lo = 0;
+        P.chunk_hi = P.total >> K;
+        P.ntasks = (P.chunk_hi + 31) / 32;
+        P.engine = PERM_ENGINE_GENERIC;
+        P.gf = gf;
+        P.nmax = nmax;
+        std::memset(&mats[i], 0, sizeof(mats[i]));
+        mats[i].task_begin = ntasks;
+        mats[i].chunk_lo = 0;
+        mats[i].chunk_hi = P.chunk_hi;
+        mats[i].K = K;
+        ntasks += P.ntasks;
+    }
+    images.assign(plans.size() * gf.devmat_bytes, 0);
+    std::vector<unsigned char> img;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        build_devmat(plans[i]->m, plans[i]->L, arith, nmax, img);
+        std::memcpy(images.data() + i * gf.devmat_bytes, img.data(), gf.devmat_bytes);
+    }
+    cudaFuncAttributes attr;
+    if (gf.attr(&attr) == cudaSuccess) regs = attr.numRegs;
+    int bps = 0;
+    cudaError_t e = gf.occ(256, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    block = 256;
+    int64_t g = (int64_t)kSMCount * std::max(bps, 1);
+    g = std::min<int64_t>(g, ((int64_t)ntasks * 32 + block - 1) / block);
+    grid = (int)std::max<int64_t>(1, g);
+    return PERM_OK;
+}
+
+size_t BatchGroup::arena_bytes() const {
+    return align256(images.size()) + align256(mats.size() * sizeof(pk::BatchMat)) +
+           align256((size_t)ntasks * words * 8) + align256(mats.size() * (size_t)words * 8) + 256;
+}
+
+void BatchGroup::bind(unsigned char *base) {
+    size_t off = 0;
+    d_images = base + off; off += align256(images.size());
+    d_mats = reinterpret_cast<pk::BatchMat *>(base + off); off += align256(mats.size() * sizeof(pk::BatchMat));
+    d_task_out = reinterpret_cast<uint64_t *>(base + off); off += align256((size_t)ntasks * words * 8);
+    d_result = reinterpret_cast<uint64_t *>(base + off); off += align256(mats.size() * (size_t)words * 8);
+    d_counters = reinterpret_cast<uint64_t *>(base + off);
+}
+
+int BatchGroup::upload(cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_images, images.data(), images.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(images)");
+    if ((e = cudaMemcpyAsync(d_mats, mats.data(), mats.size() * sizeof(pk::BatchMat), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(task table)");
+    return PERM_OK;
+}
+
+int BatchGroup::launch(cudaStream_t st, int zero_skip) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_counters, 0, 16, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    pk::BatchArgs ba;
+    ba.mats = d_mats;
+    ba.devmats = d_images;
+    ba.ntasks = ntasks;
+    ba.task_counter = reinterpret_cast<unsigned long long *>(d_counters);
+    ba.task_out = reinterpret_cast<unsigned long long *>(d_task_out);
+    ba.skip_counter = reinterpret_cast<unsigned long long *>(d_counters + 1);
+    ba.devmat_stride = gf.devmat_bytes;
+    ba.nmat = (int)mats.size();
+    ba.zero_skip = zero_skip;
+    if ((e = gf.walk(ba, grid, block, st)) != cudaSuccess) return cuda_fail(e, "batch walk launch");
+    if ((e = batch_reduce_launch(arith, d_mats, (int)mats.size(), ntasks, d_task_out, d_result, st)) != cudaSuccess)
+        return cuda_fail(e, "batch reduce launch");
+    return PERM_OK;
+}
+
+}  // namespace perm
+
+using namespace perm;
+
+extern "C" perm_status_t perm_batch_sequential(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
+                                               void *stream, perm_result_t *out) {
+    if (count < 0) return fail(PERM_ERR_SIZE, "count < 0");
+    if (count > 0 && (!mats || !out)) return fail(PERM_ERR_ARG, "NULL matrices or results");
+    for (int32_t i = 0; i < count; ++i) {
+        perm_plan_t p = nullptr;
+        perm_status_t st = perm_plan_create(&mats[i], opts, &p);
+        if (st != PERM_OK) {
+            std::memset(&out[i], 0, sizeof(out[i]));
+            out[i].status = st;
+            if (st == PERM_ERR_CUDA) return st;
+            continue;
+        }
+        st = perm_compute(p, stream, &out[i]);
+        perm_plan_destroy(p);
+        if (st == PERM_ERR_CUDA) return st;
+    }
+    return PERM_OK;
+}
+
+extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts_in,
+                                    void *stream, perm_result_t *out) {
+    if (count < 0) return fail(PERM_ERR_SIZE, "count < 0");
+    if (count == 0) return PERM_OK;
+    if (!mats || !out) return fail(PERM_ERR_ARG, "NULL matrices or results");
+    perm_opts_t opts;
+    std::memset(&opts, 0, sizeof(opts));
+    if (opts_in) opts = *opts_in;
+    if (opts.g_lo || opts.g_hi) return fail(PERM_ERR_ARG, "sub-ranges are not available in a batch");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const double t0 = now_ms();
+
+    std::vector<std::unique_ptr<perm_plan_s>> plans(count);
+    std::map<std::pair<int, int>, BatchGroup> groups;
+    std::vector<int> singles;
+    for (int32_t i = 0; i < count; ++i) {
+        plans[i].reset(new perm_plan_s());
+        perm_plan_s &P = *plans[i];
+        perm_status_t s = plan_prepare(&mats[i], &opts, P);
+        std::memset(&out[i], 0, sizeof(out[i]));
+        if (s != PERM_OK) { out[i].status = s; plans[i].reset(); continue; }
+        if (P.zero) { describe(P, &out[i]); out[i].status = PERM_OK; plans[i].reset(); continue; }
+        if (P.m.n <= 8 || P.m.n > 48) { singles.push_back(i); continue; }
+        groups[{nmax_bucket(P.m.n), P.arith}].add(i, &P);
+    }
+    const double t_prep = now_ms() - t0;
+
+    // one arena for every group
+    size_t total = 0;
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        const int K_target = opts.chunk_log2 ? opts.chunk_log2 : tuned_chunk_log2(kv.first.first, kv.first.second);
+        perm_status_t s = (perm_status_t)G.setup(kv.first.first, kv.first.second, K_target);
+        if (s != PERM_OK) return s;
+        total += G.arena_bytes();
+    }
+    DeviceArena arena;
+    if (total) {
+        cudaError_t e = arena.alloc(total);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch arena)");
+    }
+    size_t off = 0;
+    for (auto &kv : groups) {
+        kv.second.bind(arena.base + off);
+        off += kv.second.arena_bytes();
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    for (auto &kv : groups) {
+        perm_status_t s = (perm_status_t)kv.second.upload(st);
+        if (s == PERM_OK) s = (perm_status_t)kv.second.launch(st, opts.zero_skip ? 0 : 1);
+        if (s != PERM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+    }
+    cudaEventRecord(e1, st);
+    // results back in one copy per group
+    std::vector<std::vector<uint64_t>> raw;
+    raw.reserve(groups.size());
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        raw.emplace_back(G.mats.size() * (size_t)G.words + 2);
+        cudaMemcpyAsync(raw.back().data(), G.d_result, G.mats.size() * (size_t)G.words * 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(raw.back().data() + G.mats.size() * (size_t)G.words, G.d_counters, 16,
+                        cudaMemcpyDeviceToHost, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(batch)");
+    size_t gi = 0;
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        for (size_t j = 0; j < G.idx.size(); ++j) {
+            const int i = G.idx[j];
+            perm_plan_s &P = *plans[i];
+            P.grid = G.grid;
+            P.block = G.block;
+            P.regs = G.regs;
+            describe(P, &out[i]);
+            out[i].ms_kernel = ms;
+            out[i].ms_plan = t_prep / count;
+            finish_raw(P, raw[gi].data() + j * (size_t)G.words, &out[i]);
+        }
+        ++gi;
+    }
+    for (int i : singles) {
+        perm_plan_s &P = *plans[i];
+        perm_status_t s = plan_device_setup(P);
+        if (s == PERM_OK) s = plan_launch(P, st);
+        if (s == PERM_OK) {
+            cudaError_t ce = cudaStreamSynchronize(st);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
+            s = plan_finish(P, &out[i]);
+        }
+        if (s != PERM_OK) { out[i].status = s; if (s == PERM_ERR_CUDA) return s; }
+    }
+    return PERM_OK;
+}

@@ -1,0 +1,361 @@
+// codegen.cpp -- matrix-specific kernel generation and runtime compilation.
+//
+// For one ordered matrix the generator writes CUDA C++ in which (Sec. III-B):
+//   * every row of x in registers is a named slot x[s] with a compile-time
+//     index, so the register-allocation condition of Sec. III-A holds;
+//   * the inclusion/exclusion of column j (Listing 2) is a list of updates of
+//     those slots by literal values (hex-float literals: exact), with the
+//     sign either a compile-time constant (inside the unrolled block) or a
+//     per-lane +-1 (the one divergent case of Lemma 1);
+//   * the product is rebuilt through the chain of group products (core.cuh),
+//     the generalisation of Listings 3-5;
+//   * rows beyond the first k slots live in global memory at
+//     x[(slot - k) * nthreads + tid] (Listing 4's coalesced layout), touched
+//     only by columns >= c (Algorithm 4).
+// The text is compiled by NVRTC for sm_103a and loaded through the CUDA
+// driver API; kernels are cached by their source text for the life of the
+// process.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include "codegen.hpp"
+#include "plan.hpp"
+
+// Embedded copies of core.cuh and devmat.h (generated at build time).
+extern const char *perm_embedded_core_cuh;
+extern const char *perm_embedded_devmat_h;
+
+namespace perm {
+
+namespace {
+
+constexpr int kCodegenBlockLog2 = 5;
+constexpr int kCodegenBlock = 256;
+
+// ------------------------------------------------------------------ driver API via the runtime
+struct Driver {
+    CUresult (*moduleLoadData)(CUmodule *, const void *) = nullptr;
+    CUresult (*moduleGetFunction)(CUfunction *, CUmodule, const char *) = nullptr;
+    CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             CUstream, void **, void **) = nullptr;
+    CUresult (*funcGetAttribute)(int *, CUfunction_attribute, CUfunction) = nullptr;
+    CUresult (*occupancy)(int *, CUfunction, int, size_t) = nullptr;
+    CUresult (*getErrorString)(CUresult, const char **) = nullptr;
+    CUresult (*moduleUnload)(CUmodule) = nullptr;
+    bool ok = false;
+};
+
+template <class F>
+static bool entry(const char *name, F &fp) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    fp = reinterpret_cast<F>(p);
+    return true;
+}
+
+Driver &driver() {
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        d.ok = entry("cuModuleLoadData", d.moduleLoadData) && entry("cuModuleGetFunction", d.moduleGetFunction) &&
+               entry("cuLaunchKernel", d.launchKernel) && entry("cuFuncGetAttribute", d.funcGetAttribute) &&
+               entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", d.occupancy) &&
+               entry("cuGetErrorString", d.getErrorString) && entry("cuModuleUnload", d.moduleUnload);
+    });
+    return d;
+}
+
+std::string cu_err(CUresult r) {
+    const char *s = nullptr;
+    if (driver().getErrorString) driver().getErrorString(r, &s);
+    return s ? s : "unknown driver error";
+}
+
+// ------------------------------------------------------------------ source emission
+std::string lit(const perm_plan_s &P, double v) {
+    char buf[64];
+    if (P.arith == 0) {
+        std::snprintf(buf, sizeof buf, "%a", v);
+        std::string s(buf);
+        return v < 0 ? "(" + s + ")" : s;
+    }
+    std::snprintf(buf, sizeof buf, "%lld", (long long)v);
+    std::string s(buf);
+    return v < 0 ? "(" + s + ")" : s;
+}
+
+struct Emitter {
+    const perm_plan_s &P;
+    int n, k, c;
+    std::ostringstream o;
+    explicit Emitter(const perm_plan_s &p) : P(p), n(p.m.n), k(p.k), c(p.c) {}
+
+    // value of ordered column p at slot s (doubled on the exact path)
+    bool has(int p, int s) const { return (P.L.colmask[p] >> s) & 1ull; }
+    double value(int p, int s) const {
+        const int r = P.L.row_order[s], col = P.L.col_order[p];
+        return P.arith == 0 ? P.m.fval(r, col) : 2.0 * (double)P.m.ival(r, col);
+    }
+    std::string slot(int s) const {
+        if (s < k) return "x[" + std::to_string(s) + "]";
+        return "xg[" + std::to_string(s - k) + "ull * stride]";
+    }
+    // one update of slot s by column p; mode 1/-1 = static sign, 0 = runtime s
+    void update(int p, int s, int mode, const char *ind) {
+        const std::string v = lit(P, value(p, s));
+        const std::string x = slot(s);
+        if (s < k) {
+            if (mode > 0) o << ind << x << " += " << v << ";\n";
+            else if (mode < 0) o << ind << x << " -= " << v << ";\n";
+            else o << ind << x << " = A::upd_rt(" << x << ", " << v << ", s);\n";
+        } else {
+            o << ind << "{ X t = " << x << "; ";
+            if (mode > 0) o << "t += " << v << "; ";
+            else if (mode < 0) o << "t -= " << v << "; ";
+            else o << "t = A::upd_rt(t, " << v << ", s); ";
+            o << x << " = t; }\n";
+        }
+    }
+    void column(int p, int mode, const char *ind) {
+        for (int s = 0; s < n; ++s)
+            if (has(p, s)) update(p, s, mode, ind);
+    }
+    void group_product(int g, const char *ind) {
+        for (int s = P.L.group_begin[g]; s < P.L.group_begin[g + 1]; ++s)
+            o << ind << "q = A::mul(q, " << slot(s) << ");\n";
+    }
+    // nonempty chain levels >= B, descending
+    std::vector<int> high_levels(int B) const {
+        std::vector<int> v;
+        for (int g = n - 1; g >= B; --g)
+            if (P.L.group_begin[g + 1] > P.L.group_begin[g]) v.push_back(g);
+        return v;
+    }
+
+    std::string emit() {
+        const int B = kCodegenBlockLog2;
+        const std::vector<int> hi = high_levels(B);
+        o << "// generated: permanent walk for one " << n << "x" << n << " matrix\n";
+        o << "// order=" << P.L.ordering << " reg_rows(k)=" << k << " reg_cols(c)=" << c << " B=" << B << "\n";
+        o << "#include \"core.cuh\"\n\nnamespace pk {\n";
+        if (P.arith == 0) o << "typedef ArithF64 A;\n";
+        else o << "typedef ArithExact<" << P.arith << "> A;\n";
+        o << "struct GenPol {\n";
+        o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
+        o << "    typedef A::X X;\n    typedef A::P P;\n";
+        o << "    X *xg;\n    unsigned long long stride;\n";
+        for (int g : hi) o << "    P Q" << g << ";\n";
+        // flips inside the unrolled block (static column, static or runtime sign)
+        o << "    template <int J, int S> __device__ __forceinline__ void flip(X (&x)[NX]) {\n";
+        for (int p = 0; p < B && p < n - 1; ++p) {
+            o << "        " << (p ? "else " : "") << "if constexpr (J == " << p << ") {\n";
+            o << "            if constexpr (S > 0) {\n";
+            column(p, 1, "                ");
+            o << "            } else {\n";
+            column(p, -1, "                ");
+            o << "            }\n        }\n";
+        }
+        o << "    }\n";
+        o << "    template <int J> __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) {\n";
+        for (int p = 0; p < B && p < n - 1; ++p) {
+            o << "        " << (p ? "else " : "") << "if constexpr (J == " << p << ") {\n";
+            column(p, 0, "            ");
+            o << "        }\n";
+        }
+        o << "    }\n";
+        // a flip chosen at run time (block boundaries, start vectors)
+        o << "    __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {\n";
+        o << "        switch (j) {\n";
+        for (int p = 0; p < n - 1; ++p) {
+            o << "        case " << p << ":\n";
+            column(p, 0, "            ");
+            o << "            break;\n";
+        }
+        o << "        default: break;\n        }\n    }\n";
+        // group products of the low levels
+        o << "    template <int M> __device__ __forceinline__ P grp(const X (&x)[NX], P q) const {\n";
+        for (int g = 0; g < B; ++g) {
+            o << "        " << (g ? "else " : "") << "if constexpr (M == " << g << ") {\n";
+            if (g < n) group_product(g, "            ");
+            o << "        }\n";
+        }
+        o << "        return q;\n    }\n";
+        // start vector
+        o << "    __device__ __forceinline__ void init_x(X (&x)[NX], unsigned long long G) {\n";
+        const int last = P.L.col_order[n - 1];
+        for (int s = 0; s < n; ++s) {
+            const int r = P.L.row_order[s];
+            double x0;
+            if (P.arith == 0) {
+                double rowsum = 0.0;
+                for (int j = 0; j < n; ++j) rowsum += P.m.fval(r, j);
+                x0 = P.m.fval(r, last) - rowsum / 2.0;
+            } else {
+                int64_t rowsum = 0;
+                for (int j = 0; j < n; ++j) rowsum += P.m.ival(r, j);
+                x0 = (double)(2 * P.m.ival(r, last) - rowsum);
+            }
+            o << "        " << slot(s) << " = " << lit(P, x0) << ";\n";
+        }
+        for (int s = n; s < k; ++s) o << "        x[" << s << "] = 0;\n";
+        o << "        while (G) {\n            const int p = ctz64(G);\n            G &= G - 1;\n";
+        o << "            flip_dyn(p, x, 1);\n        }\n    }\n";
+        // high chain levels
+        auto above = [&](int g) -> std::string {   // the nonempty level just above g
+            for (int h = g + 1; h < n; ++h)
+                if (P.L.group_begin[h + 1] > P.L.group_begin[h] && h >= B) return "Q" + std::to_string(h);
+            return "A::one()";
+        };
+        o << "    __device__ __forceinline__ P chain_init(const X (&x)[NX]) {\n";
+        o << "        P q = A::one();\n";
+        for (int g : hi) {
+            group_product(g, "        ");
+            o << "        Q" << g << " = q;\n";
+        }
+        o << "        return q;\n    }\n";
+        o << "    __device__ __forceinline__ P chain_hi(int j, const X (&x)[NX]) {\n";
+        o << "        P q;\n        switch (j) {\n";
+        for (int j = B; j < n - 1; ++j) {
+            o << "        case " << j << ":\n";
+            o << "            q = " << above(j) << ";\n";
+            for (int g : hi) {
+                if (g > j) continue;
+                group_product(g, "            ");
+                o << "            Q" << g << " = q;\n";
+            }
+            o << "            return q;\n";
+        }
+        o << "        default: return " << (hi.empty() ? std::string("A::one()") : "Q" + std::to_string(hi.back()))
+          << ";\n        }\n    }\n";
+        o << "};\n}  // namespace pk\n\n";
+        o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock
+          << ") perm_walk(pk::WalkArgs wa, void *xg_base) {\n";
+        o << "    pk::GenPol pol;\n";
+        o << "    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
+        o << "    pol.stride = (unsigned long long)gridDim.x * blockDim.x;\n";
+        o << "    pol.xg = reinterpret_cast<pk::GenPol::X *>(xg_base) + tid;\n";
+        o << "    pk::walk_tasks<pk::GenPol, pk::A, " << B << ">(pol, wa);\n}\n";
+        return o.str();
+    }
+};
+
+// ------------------------------------------------------------------ cache
+struct CacheEntry {
+    CUmodule module = nullptr;
+    CUfunction function = nullptr;
+    int regs = 0;
+    int blocks_per_sm = 0;
+};
+
+std::mutex g_cache_mu;
+std::unordered_map<std::string, CacheEntry> g_cache;
+constexpr size_t kCacheMax = 512;
+
+}  // namespace
+
+std::string codegen_source(const perm_plan_s &P) {
+    Emitter e(P);
+    return e.emit();
+}
+
+perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
+    Driver &d = driver();
+    if (!d.ok) { err = "CUDA driver entry points unavailable"; return PERM_ERR_CUDA; }
+    const std::string src = codegen_source(P);
+    P.cg.block = kCodegenBlock;
+    P.cg.block_log2 = kCodegenBlockLog2;
+    const bool use_cache = !(P.opts.flags & PERM_FLAG_NO_KERNEL_CACHE);
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_cache.find(src);
+        if (it != g_cache.end()) {
+            P.cg.module = it->second.module;
+            P.cg.function = it->second.function;
+            P.cg.regs = it->second.regs;
+            P.cg.blocks_per_sm = it->second.blocks_per_sm;
+            P.cg.cached = true;
+            P.regs = P.cg.regs;
+            P.ms_compile = 0.0;
+            return PERM_OK;
+        }
+    }
+    const double t0 = now_ms();
+    nvrtcProgram prog;
+    const char *hdr_src[2] = {perm_embedded_core_cuh, perm_embedded_devmat_h};
+    const char *hdr_name[2] = {"core.cuh", "devmat.h"};
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "perm_walk.cu", 2, hdr_src, hdr_name);
+    if (r != NVRTC_SUCCESS) { err = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r); return PERM_ERR_NVRTC; }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--device-as-default-execution-space"};
+    r = nvrtcCompileProgram(prog, 4, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nvrtcGetProgramLogSize(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) nvrtcGetProgramLog(prog, &log[0]);
+        nvrtcDestroyProgram(&prog);
+        err = "NVRTC compile failed: " + log.substr(0, 2000);
+        return PERM_ERR_NVRTC;
+    }
+    size_t cs = 0;
+    nvrtcGetCUBINSize(prog, &cs);
+    std::vector<char> cubin(cs);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    cudaFree(nullptr);   // make the primary context current on this thread
+    CacheEntry ce;
+    CUresult cr = d.moduleLoadData(&ce.module, cubin.data());
+    if (cr != CUDA_SUCCESS) { err = "cuModuleLoadData: " + cu_err(cr); return PERM_ERR_CUDA; }
+    cr = d.moduleGetFunction(&ce.function, ce.module, "perm_walk");
+    if (cr != CUDA_SUCCESS) { err = "cuModuleGetFunction: " + cu_err(cr); return PERM_ERR_CUDA; }
+    d.funcGetAttribute(&ce.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ce.function);
+    cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, 0);
+    if (cr != CUDA_SUCCESS) { err = "occupancy: " + cu_err(cr); return PERM_ERR_CUDA; }
+    P.ms_compile = now_ms() - t0;
+    if (use_cache) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (g_cache.size() < kCacheMax) g_cache.emplace(src, ce);
+        else P.cg.owned = true;
+    } else {
+        P.cg.owned = true;
+    }
+    P.cg.module = ce.module;
+    P.cg.function = ce.function;
+    P.cg.regs = ce.regs;
+    P.cg.blocks_per_sm = ce.blocks_per_sm;
+    P.cg.cached = false;
+    P.regs = ce.regs;
+    return PERM_OK;
+}
+
+cudaError_t codegen_launch(perm_plan_s &P, const pk::WalkArgs &wa, cudaStream_t st) {
+    Driver &d = driver();
+    pk::WalkArgs a = wa;
+    void *xg = P.d_xglob;
+    void *params[] = {&a, &xg};
+    CUresult r = d.launchKernel(reinterpret_cast<CUfunction>(P.cg.function), (unsigned)P.grid, 1, 1,
+                                (unsigned)P.block, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+void codegen_release(perm_plan_s &P) {
+    // cached modules live as long as the process; uncached ones go with the plan
+    if (P.cg.owned && P.cg.module && driver().moduleUnload)
+        driver().moduleUnload(reinterpret_cast<CUmodule>(P.cg.module));
+    P.cg.module = nullptr;
+    P.cg.function = nullptr;
+}
+
+}  // namespace perm

@@ -1,0 +1,370 @@
+// core.cuh -- the Gray-code walk shared by every enumeration kernel.
+//
+// This header is compiled twice: by nvcc into the precompiled generic kernels
+// (generic.cu) and, as source text, by NVRTC into every per-matrix kernel the
+// code generator emits.  It therefore uses no standard headers.
+//
+// The walk (Algorithm 1, Nijenhuis-Wilf variant of Eq. 2).  The columns are in
+// the plan's order, column n-1 is never flipped, and x is
+//     x_i(g) = x0_i + sum_{j : bit j of Gray(g)} a_ij,
+//     x0_i   = a_{i,n-1} - (1/2) sum_j a_ij            (FP64 path)
+// or twice that (exact path, so that x stays integral).  Gray index g
+// contributes (-1)^g prod_i x_i(g).
+//
+// Parallel layout (Sec. II-A, Theorem 1, Lemma 1).  The 2^(n-1) indices are
+// cut into aligned chunks of 2^K; chunk q starts from x(q 2^K), built from the
+// set bits of Gray(q 2^K) (all >= K-1).  Inside a chunk step l flips column
+// j = ctz(l) with sign + iff bit j+1 of g is 0 (Theorem 1).  Because chunks are
+// aligned powers of two, every lane of a warp flips the same column at the same
+// step: only the sign of column K-1 differs between lanes (the first case of
+// Lemma 1), and that is an arithmetic sign, not a branch.  The second
+// divergent case of Lemma 1 (l = 2^k) never arises because each chunk starts
+// from its own start vector.  Chunks are grouped 32 per warp task; warps of a
+// persistent grid take tasks from an atomic counter.
+//
+// Blocks.  A chunk is walked in blocks of 2^B steps.  The 2^B - 1 flips inside
+// a block are columns 0..B-1 in the ruler order of SCBS(B) (Sec. IV) and are
+// fully unrolled with compile-time column, row set and sign; only the flip at
+// a block boundary (column >= B) is chosen at run time, and it is uniform
+// across the warp.
+//
+// Product chain.  Rows are grouped by the first ordered column that touches
+// them: R_m.  A flip of column j changes only rows in R_0..R_j, so with
+//     Q_m = prod of x over R_m, R_{m+1}, ..., R_{n-1}
+// the product after the flip is Q_0, rebuilt from Q_{j+1} by |R_0|+...+|R_j|
+// multiplications.  This generalises the reuse of globalProduct for
+// register-only columns (Sec. V, Listings 4-5) to every level, and with the
+// permanent ordering of Algorithm 3 the low levels hold few rows.  Every term
+// is still the product of the same n numbers; only the association changes.
+//
+// Zero skip (Sec. VI-B's zero tracking, made warp-uniform).  When Q_B is zero
+// in every lane at a block boundary, all 2^B products of the block are zero:
+// the block is replaced by its net effect on x (one flip of column B-1).
+#pragma once
+
+#include "devmat.h"
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+typedef long long i64;
+
+#ifndef PERM_FULLMASK
+#define PERM_FULLMASK 0xffffffffu
+#endif
+
+namespace pk {
+
+__device__ __forceinline__ int ctz64(u64 v) { return __ffsll((long long)v) - 1; }
+
+// ------------------------------------------------------------------ FP64 arithmetic
+
+struct ArithF64 {
+    typedef double X;   // an entry of x
+    typedef double P;   // a (partial) product
+    typedef double V;   // a matrix value as stored
+    struct Acc { double hi, lo; };
+    static __device__ __forceinline__ P one() { return 1.0; }
+    static __device__ __forceinline__ P mul(P q, X x) { return q * x; }
+    static __device__ __forceinline__ bool is_zero(P q) { return q == 0.0; }
+    template <int S> static __device__ __forceinline__ X upd(X x, V v) { return S > 0 ? x + v : x - v; }
+    static __device__ __forceinline__ X upd_rt(X x, V v, int s) { return fma((double)s, v, x); }
+    // block accumulator: a plain double over 2^B terms
+    typedef double Blk;
+    static __device__ __forceinline__ Blk blk_zero() { return 0.0; }
+    template <int S> static __device__ __forceinline__ void blk_add(Blk &b, P p) { if (S > 0) b += p; else b -= p; }
+    static __device__ __forceinline__ Acc acc_zero() { Acc a; a.hi = 0.0; a.lo = 0.0; return a; }
+    // TwoSum (Knuth): a.hi + b = s + e exactly
+    static __device__ __forceinline__ void acc_merge(Acc &a, Blk b) {
+        double s = a.hi + b;
+        double bb = s - a.hi;
+        double e = (a.hi - (s - bb)) + (b - bb);
+        a.hi = s;
+        a.lo += e;
+    }
+    static __device__ __forceinline__ Acc acc_add(Acc a, Acc b) {
+        double s = a.hi + b.hi;
+        double bb = s - a.hi;
+        double e = (a.hi - (s - bb)) + (b.hi - bb);
+        e += a.lo + b.lo;
+        Acc r;
+        r.hi = s + e;
+        r.lo = e - (r.hi - s);
+        return r;
+    }
+    static __device__ __forceinline__ Acc shfl_down(Acc a, int d) {
+        Acc r;
+        r.hi = __shfl_down_sync(PERM_FULLMASK, a.hi, d);
+        r.lo = __shfl_down_sync(PERM_FULLMASK, a.lo, d);
+        return r;
+    }
+    static constexpr int ACC_WORDS = 2;   // stored as two doubles
+    static __device__ __forceinline__ void acc_store(u64 *dst, Acc a) {
+        dst[0] = (u64)__double_as_longlong(a.hi);
+        dst[1] = (u64)__double_as_longlong(a.lo);
+    }
+    static __device__ __forceinline__ Acc acc_load(const u64 *src) {
+        Acc a;
+        a.hi = __longlong_as_double((long long)src[0]);
+        a.lo = __longlong_as_double((long long)src[1]);
+        return a;
+    }
+};
+
+// ------------------------------------------------------------------ exact arithmetic
+// Products live in Z / 2^(32 L): L little-endian 32-bit limbs.  x entries are
+// signed 32-bit (twice the Nijenhuis-Wilf row sums).  Wrapping arithmetic is a
+// ring homomorphism, so the final sum is exact modulo 2^(32 L).
+
+template <int L> struct Ring { u32 w[L]; };
+
+template <int L>
+__device__ __forceinline__ Ring<L> ring_mul(const Ring<L> &q, int x) {
+    // q * (x mod 2^32), then subtract q * 2^32 when x < 0 (two's complement).
+    Ring<L> r;
+    u32 m = (u32)x;
+    u64 c = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u64 t = (u64)q.w[i] * m + c;
+        r.w[i] = (u32)t;
+        c = t >> 32;
+    }
+    if (x < 0) {
+        u32 borrow = 0;
+#pragma unroll
+        for (int i = 1; i < L; ++i) {
+            u64 t = (u64)r.w[i] - (u64)q.w[i - 1] - (u64)borrow;
+            r.w[i] = (u32)t;
+            borrow = (u32)(t >> 63);
+        }
+    }
+    return r;
+}
+
+template <>
+__device__ __forceinline__ Ring<2> ring_mul<2>(const Ring<2> &q, int x) {
+    u64 v = ((u64)q.w[1] << 32) | q.w[0];
+    v *= (u64)(i64)x;
+    Ring<2> r;
+    r.w[0] = (u32)v;
+    r.w[1] = (u32)(v >> 32);
+    return r;
+}
+
+template <int L>
+__device__ __forceinline__ void ring_add(Ring<L> &a, const Ring<L> &b) {
+    u32 c = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u64 t = (u64)a.w[i] + b.w[i] + c;
+        a.w[i] = (u32)t;
+        c = (u32)(t >> 32);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void ring_sub(Ring<L> &a, const Ring<L> &b) {
+    u32 br = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u64 t = (u64)a.w[i] - (u64)b.w[i] - (u64)br;
+        a.w[i] = (u32)t;
+        br = (u32)(t >> 63);
+    }
+}
+
+template <>
+__device__ __forceinline__ void ring_add<2>(Ring<2> &a, const Ring<2> &b) {
+    u64 v = (((u64)a.w[1] << 32) | a.w[0]) + (((u64)b.w[1] << 32) | b.w[0]);
+    a.w[0] = (u32)v;
+    a.w[1] = (u32)(v >> 32);
+}
+
+template <>
+__device__ __forceinline__ void ring_sub<2>(Ring<2> &a, const Ring<2> &b) {
+    u64 v = (((u64)a.w[1] << 32) | a.w[0]) - (((u64)b.w[1] << 32) | b.w[0]);
+    a.w[0] = (u32)v;
+    a.w[1] = (u32)(v >> 32);
+}
+
+template <int W>   // W 64-bit words = 2W limbs
+struct ArithExact {
+    static constexpr int L = 2 * W;
+    typedef int X;
+    typedef Ring<L> P;
+    typedef int V;
+    typedef Ring<L> Acc;
+    typedef Ring<L> Blk;
+    static __device__ __forceinline__ P one() {
+        P r;
+#pragma unroll
+        for (int i = 0; i < L; ++i) r.w[i] = 0;
+        r.w[0] = 1;
+        return r;
+    }
+    static __device__ __forceinline__ P mul(const P &q, X x) { return ring_mul<L>(q, x); }
+    static __device__ __forceinline__ bool is_zero(const P &q) {
+        u32 o = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) o |= q.w[i];
+        return o == 0;
+    }
+    template <int S> static __device__ __forceinline__ X upd(X x, V v) { return S > 0 ? x + v : x - v; }
+    static __device__ __forceinline__ X upd_rt(X x, V v, int s) { return x + s * v; }
+    static __device__ __forceinline__ Blk blk_zero() {
+        Blk r;
+#pragma unroll
+        for (int i = 0; i < L; ++i) r.w[i] = 0;
+        return r;
+    }
+    template <int S> static __device__ __forceinline__ void blk_add(Blk &b, const P &p) {
+        if (S > 0) ring_add<L>(b, p); else ring_sub<L>(b, p);
+    }
+    static __device__ __forceinline__ Acc acc_zero() { return blk_zero(); }
+    static __device__ __forceinline__ void acc_merge(Acc &a, const Blk &b) { ring_add<L>(a, b); }
+    static __device__ __forceinline__ Acc acc_add(Acc a, const Acc &b) { ring_add<L>(a, b); return a; }
+    static __device__ __forceinline__ Acc shfl_down(const Acc &a, int d) {
+        Acc r;
+#pragma unroll
+        for (int i = 0; i < L; ++i) r.w[i] = __shfl_down_sync(PERM_FULLMASK, a.w[i], d);
+        return r;
+    }
+    static constexpr int ACC_WORDS = W;
+    static __device__ __forceinline__ void acc_store(u64 *dst, const Acc &a) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) dst[i] = ((u64)a.w[2 * i + 1] << 32) | a.w[2 * i];
+    }
+    static __device__ __forceinline__ Acc acc_load(const u64 *src) {
+        Acc a;
+#pragma unroll
+        for (int i = 0; i < W; ++i) { a.w[2 * i] = (u32)src[i]; a.w[2 * i + 1] = (u32)(src[i] >> 32); }
+        return a;
+    }
+};
+
+// ------------------------------------------------------------------ the unrolled block
+// Step l (1 <= l < 2^B) of a block flips column J = ctz(l).  Its sign is bit
+// J+1 of l for J < B-1; for J = B-1 it is bit B of the block start, passed in
+// as s_mid.  The term's sign (-1)^g equals (-1)^l because every block starts
+// at an even index.
+
+template <int Lstep> struct Ctz { static constexpr int v = (Lstep & 1) ? 0 : 1 + Ctz<(Lstep >> 1)>::v; };
+template <> struct Ctz<0> { static constexpr int v = 0; };
+
+// Rebuilds chain levels M, M-1, ..., 1 (Q[m] = Q[m+1] * prod over R_m).
+template <class Pol, class A, int Bv, int M>
+struct LevelsDown {
+    static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1]) {
+        if constexpr (M >= 1) {
+            Q[M] = pol.template grp<M>(x, Q[M + 1]);
+            LevelsDown<Pol, A, Bv, M - 1>::run(pol, x, Q);
+        }
+    }
+};
+
+template <class Pol, class A, int Bv, int Lstep>
+struct BlockSteps {
+    static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
+                                               typename A::Blk &blk, int s_mid) {
+        if constexpr (Lstep < (1 << Bv)) {
+            constexpr int J = Ctz<Lstep>::v;
+            if constexpr (J == Bv - 1) {
+                pol.template flip_rt<J>(x, s_mid);
+            } else {
+                constexpr int S = ((Lstep >> (J + 1)) & 1) ? -1 : 1;
+                pol.template flip<J, S>(x);
+            }
+            LevelsDown<Pol, A, Bv, J>::run(pol, x, Q);
+            typename A::P p = pol.template grp<0>(x, Q[1]);
+            A::template blk_add<(Lstep & 1) ? -1 : 1>(blk, p);
+            BlockSteps<Pol, A, Bv, Lstep + 1>::run(pol, x, Q, blk, s_mid);
+        }
+    }
+};
+
+// ------------------------------------------------------------------ one chunk
+// Walks Gray indices [q 2^K, (q+1) 2^K) and returns sum (-1)^g prod_i x_i(g).
+
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
+    typedef typename A::X X;
+    typedef typename A::P P;
+    X x[Pol::NX];
+    const u64 g0 = q << K;
+    pol.init_x(x, g0 ^ (g0 >> 1));
+    P QB = pol.chain_init(x);
+    typename A::Acc acc = A::acc_zero();
+    const u64 nblocks = 1ull << (K - Bv);
+    for (u64 h = 0; h < nblocks; ++h) {
+        const u64 gb = g0 + (h << Bv);
+        if (h != 0) {
+            const int j = Bv + ctz64(h);
+            const int s = ((gb >> (j + 1)) & 1ull) ? -1 : 1;
+            pol.flip_dyn(j, x, s);
+            QB = pol.chain_hi(j, x);
+        }
+        const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
+        if (zero_skip && __all_sync(PERM_FULLMASK, A::is_zero(QB))) {
+            // every product of this block is zero; apply the block's net flip
+            pol.template flip_rt<Bv - 1>(x, s_mid);
+            ++skipped;
+            continue;
+        }
+        P Q[Bv + 1];
+        Q[Bv] = QB;
+        LevelsDown<Pol, A, Bv, Bv - 1>::run(pol, x, Q);
+        typename A::Blk blk = A::blk_zero();
+        A::template blk_add<1>(blk, pol.template grp<0>(x, Q[1]));
+        BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
+        A::acc_merge(acc, blk);
+    }
+    return acc;
+}
+
+// ------------------------------------------------------------------ persistent warp loop
+
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ void walk_tasks(Pol &pol, const WalkArgs &wa) {
+    const int lane = threadIdx.x & 31;
+    u64 skipped = 0;
+    for (;;) {
+        u64 task = 0;
+        if (lane == 0) task = atomicAdd(wa.task_counter, 1ull);
+        task = __shfl_sync(PERM_FULLMASK, task, 0);
+        if (task >= wa.ntasks) break;
+        u64 q = wa.chunk_lo + task * 32ull + (u64)lane;
+        const bool live = q < wa.chunk_hi;
+        if (!live) q = wa.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
+        typename A::Acc acc = walk_chunk<Pol, A, Bv>(pol, q, wa.K, wa.zero_skip, skipped);
+        if (!live) acc = A::acc_zero();
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+        if (lane == 0) A::acc_store(wa.task_out + task * (u64)A::ACC_WORDS, acc);
+    }
+    if (wa.skip_counter && lane == 0 && skipped) atomicAdd(wa.skip_counter, skipped);
+}
+
+// ------------------------------------------------------------------ final reduction
+// One block sums the task results in a fixed order (deterministic).
+
+template <class A>
+__device__ __forceinline__ void reduce_tasks(const u64 *task_out, u64 ntasks, u64 *result) {
+    __shared__ u64 sh[32 * 6];
+    typename A::Acc acc = A::acc_zero();
+    for (u64 t = threadIdx.x; t < ntasks; t += blockDim.x)
+        acc = A::acc_add(acc, A::acc_load(task_out + t * (u64)A::ACC_WORDS));
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) A::acc_store(sh + warp * A::ACC_WORDS, acc);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        acc = lane < nw ? A::acc_load(sh + lane * A::ACC_WORDS) : A::acc_zero();
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+        if (lane == 0) A::acc_store(result, acc);
+    }
+}
+
+}  // namespace pk

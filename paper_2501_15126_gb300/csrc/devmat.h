@@ -1,0 +1,59 @@
+// devmat.h -- plain-old-data shared by the host code and the kernels (and
+// handed to NVRTC as a header of the generated kernels): the launch
+// arguments of the walk and the matrix image read by the generic kernels.
+// No standard headers, so NVRTC can compile it as is.
+#pragma once
+
+namespace pk {
+
+// Launch arguments of one Gray-code walk (see core.cuh).
+struct WalkArgs {
+    unsigned long long chunk_lo;        // first chunk index (in units of 2^K Gray indices)
+    unsigned long long chunk_hi;        // one past the last chunk index
+    unsigned long long ntasks;          // ceil((chunk_hi - chunk_lo) / 32): one task = 32 chunks
+    unsigned long long *task_counter;   // zeroed before the launch; warps take tasks from it
+    unsigned long long *task_out;       // ntasks * words: one warp-reduced result per task
+    unsigned long long *skip_counter;   // blocks skipped as all-zero (may be null)
+    int K;                              // log2 of the chunk length (>= B)
+    int zero_skip;                      // 1 = skip all-zero blocks
+};
+
+// One matrix of a generic (multi-matrix) walk: its tasks are
+// [task_begin, task_begin + ceil((chunk_hi - chunk_lo) / 32)).
+struct BatchMat {
+    unsigned long long task_begin;
+    unsigned long long chunk_lo;
+    unsigned long long chunk_hi;
+    int K;
+    int pad;
+};
+
+// Launch arguments of the generic kernels: any number of matrices of one
+// NMAX bucket and one arithmetic, their images packed devmat_stride apart.
+struct BatchArgs {
+    const BatchMat *mats;
+    const void *devmats;
+    unsigned long long ntasks;          // sum of all matrices' tasks
+    unsigned long long *task_counter;   // zeroed before the launch
+    unsigned long long *task_out;       // ntasks * words
+    unsigned long long *skip_counter;   // may be null
+    unsigned long long devmat_stride;   // bytes between consecutive images
+    int nmat;
+    int zero_skip;
+};
+
+// The ordered matrix as the generic kernels read it (shared memory image).
+// Slots are rows in the plan's order; positions are columns in the plan's
+// order.  V is double (FP64 path) or int (exact path: values doubled).
+template <int NMAX, typename V>
+struct DevMat {
+    int n;                              // dimension
+    int top;                            // highest nonempty row group
+    int pad0, pad1;
+    unsigned long long colmask[NMAX];   // slots touched by column position p (p < n-1)
+    unsigned long long grpmask[NMAX];   // slots whose first touching column is m
+    V x0[NMAX];                         // Nijenhuis-Wilf start values by slot
+    V val[NMAX * NMAX];                 // val[p * NMAX + slot] = value of column p at slot
+};
+
+}  // namespace pk

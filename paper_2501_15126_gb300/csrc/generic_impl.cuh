@@ -1,0 +1,270 @@
+// generic_impl.cuh -- precompiled enumeration kernels (no per-matrix compilation).
+//
+// The walk of core.cuh with a matrix policy that reads the ordered matrix
+// from shared memory: a column flip or a group product runs over all NMAX
+// register slots with a warp-uniform predicate from the column's (group's)
+// bitmask, so every x index is a compile-time constant and x stays in
+// registers (the register-allocation condition of Sec. III-A) without knowing
+// the sparsity pattern at compile time.  The unrolled block is 2^B steps with
+// B = PERM_GENERIC_B.  Each generic_<arith>.cu file instantiates these
+// templates for one arithmetic and every NMAX bucket; the build compiles the
+// files in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "core.cuh"
+#include "kernels.hpp"
+
+#ifndef PERM_GENERIC_B
+#define PERM_GENERIC_B 4
+#endif
+
+namespace pk {
+
+template <int NMAX, class A>
+struct GenericPol {
+    static constexpr int NX = NMAX;
+    static constexpr int Bv = PERM_GENERIC_B;
+    typedef typename A::X X;
+    typedef typename A::P P;
+    typedef typename A::V V;
+    typedef DevMat<NMAX, V> M;
+
+    const M *m;
+    P Qh[NMAX + 1];     // chain levels >= B (dynamic index: local memory)
+
+    __device__ __forceinline__ explicit GenericPol(const M *mat) : m(mat) {}
+
+    template <int J, int S>
+    __device__ __forceinline__ void flip(X (&x)[NX]) {
+        const u64 cm = ((const volatile u64 *)m->colmask)[J];
+        const volatile V *v = m->val + J * NMAX;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if ((cm >> i) & 1ull) x[i] = A::template upd<S>(x[i], v[i]);
+    }
+    template <int J>
+    __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) {
+        const u64 cm = ((const volatile u64 *)m->colmask)[J];
+        const volatile V *v = m->val + J * NMAX;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], v[i], s);
+    }
+    __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {
+        const u64 cm = ((const volatile u64 *)m->colmask)[j];
+        const volatile V *v = m->val + j * NMAX;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], v[i], s);
+    }
+    template <int G>
+    __device__ __forceinline__ P grp(const X (&x)[NX], P q) const {
+        const u64 gm = ((const volatile u64 *)m->grpmask)[G];
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if ((gm >> i) & 1ull) q = A::mul(q, x[i]);
+        return q;
+    }
+    __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
+        const u64 gm = ((const volatile u64 *)m->grpmask)[g];
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if ((gm >> i) & 1ull) q = A::mul(q, x[i]);
+        return q;
+    }
+    // x = x0 + sum of the columns set in Gray code G (columns < n-1 only)
+    __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) x[i] = m->x0[i];
+        while (G) {
+            const int p = ctz64(G);
+            G &= G - 1;
+            flip_dyn(p, x, 1);
+        }
+    }
+    // all levels from the top group down to B
+    __device__ __forceinline__ P chain_init(const X (&x)[NX]) {
+        const int top = m->top;
+        P q = A::one();
+        for (int g = NMAX; g > top; --g) Qh[g] = q;
+        for (int g = top; g >= Bv; --g) {
+            q = grp_dyn(g, x, q);
+            Qh[g] = q;
+        }
+        return top >= Bv ? Qh[Bv] : q;
+    }
+    // after a flip of column j >= B: levels j..B
+    __device__ __forceinline__ P chain_hi(int j, const X (&x)[NX]) {
+        P q = Qh[j + 1];
+        for (int g = j; g >= Bv; --g) {
+            q = grp_dyn(g, x, q);
+            Qh[g] = q;
+        }
+        return q;
+    }
+};
+
+// The generic walk over any number of matrices (a single matrix is a batch
+// of one).  Warps of a persistent grid take 32-chunk tasks from one counter;
+// a task's matrix is found by binary search over the task ranges, and the
+// warp stages that matrix's image in its own shared-memory slot (restaged
+// only when the matrix changes).
+template <int NMAX, class A>
+__global__ void __launch_bounds__(256) k_walk_generic(BatchArgs ba) {
+    typedef DevMat<NMAX, typename A::V> M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    M *slot = reinterpret_cast<M *>(smem_raw + (size_t)warp * sizeof(M));
+    int cached = -1;
+    u64 skipped = 0;
+    for (;;) {
+        u64 task = 0;
+        if (lane == 0) task = atomicAdd(ba.task_counter, 1ull);
+        task = __shfl_sync(PERM_FULLMASK, task, 0);
+        if (task >= ba.ntasks) break;
+        int m = 0;
+        if (lane == 0) {
+            int lo = 0, hi = ba.nmat - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ba.mats[mid].task_begin <= task) lo = mid; else hi = mid - 1;
+            }
+            m = lo;
+        }
+        m = __shfl_sync(PERM_FULLMASK, m, 0);
+        if (m != cached) {
+            __syncwarp();
+            const uint4 *src = reinterpret_cast<const uint4 *>(
+                reinterpret_cast<const unsigned char *>(ba.devmats) + (size_t)m * ba.devmat_stride);
+            uint4 *dst = reinterpret_cast<uint4 *>(slot);
+            for (int i = lane; i < (int)(sizeof(M) / 16); i += 32) dst[i] = src[i];
+            __syncwarp();
+            cached = m;
+        }
+        const BatchMat bm = ba.mats[m];
+        u64 q = bm.chunk_lo + (task - bm.task_begin) * 32ull + (u64)lane;
+        const bool live = q < bm.chunk_hi;
+        if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
+        GenericPol<NMAX, A> pol(slot);
+        typename A::Acc acc = walk_chunk<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
+        if (!live) acc = A::acc_zero();
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+        if (lane == 0) A::acc_store(ba.task_out + task * (u64)A::ACC_WORDS, acc);
+    }
+    if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
+}
+
+// Tiny matrices: one thread per Gray index, x built from scratch.
+template <int NMAX, class A>
+__global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typename A::V> *m, u64 g_lo, u64 g_hi,
+                                                        u64 *block_out) {
+    typedef typename A::X X;
+    const u64 g = g_lo + (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    typename A::Acc acc = A::acc_zero();
+    if (g < g_hi) {
+        X x[NMAX];
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) x[i] = m->x0[i];
+        u64 G = g ^ (g >> 1);
+        while (G) {
+            const int p = ctz64(G);
+            G &= G - 1;
+            const u64 cm = m->colmask[p];
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i)
+                if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], m->val[p * NMAX + i], 1);
+        }
+        typename A::P q = A::one();
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if (i < m->n) q = A::mul(q, x[i]);
+        typename A::Blk b = A::blk_zero();
+        if (g & 1ull) A::template blk_add<-1>(b, q); else A::template blk_add<1>(b, q);
+        A::acc_merge(acc, b);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+    __shared__ u64 sh[8 * 6];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) A::acc_store(sh + warp * A::ACC_WORDS, acc);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        acc = lane < nw ? A::acc_load(sh + lane * A::ACC_WORDS) : A::acc_zero();
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+        if (lane == 0) A::acc_store(block_out + (u64)blockIdx.x * A::ACC_WORDS, acc);
+    }
+}
+
+}  // namespace pk
+
+namespace perm {
+
+template <int NMAX, class A>
+static size_t smem_walk_t(int block) {
+    return (size_t)(block / 32) * sizeof(pk::DevMat<NMAX, typename A::V>);
+}
+
+template <int NMAX, class A>
+static cudaError_t launch_walk_t(const pk::BatchArgs &ba, int grid, int block, cudaStream_t st) {
+    const size_t smem = smem_walk_t<NMAX, A>(block);
+    cudaError_t e = cudaFuncSetAttribute(pk::k_walk_generic<NMAX, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    pk::k_walk_generic<NMAX, A><<<grid, block, smem, st>>>(ba);
+    return cudaGetLastError();
+}
+
+template <int NMAX, class A>
+static cudaError_t launch_direct_t(const void *devmat, uint64_t g_lo, uint64_t g_hi, uint64_t *out, int grid,
+                                   int block, cudaStream_t st) {
+    pk::k_direct_generic<NMAX, A><<<grid, block, 0, st>>>(
+        reinterpret_cast<const pk::DevMat<NMAX, typename A::V> *>(devmat), g_lo, g_hi,
+        reinterpret_cast<unsigned long long *>(out));
+    return cudaGetLastError();
+}
+
+template <int NMAX, class A>
+static cudaError_t attr_walk_t(cudaFuncAttributes *attr) {
+    return cudaFuncGetAttributes(attr, pk::k_walk_generic<NMAX, A>);
+}
+
+template <int NMAX, class A>
+static cudaError_t occ_walk_t(int block, int *blocks_per_sm) {
+    const size_t smem = smem_walk_t<NMAX, A>(block);
+    cudaError_t e = cudaFuncSetAttribute(pk::k_walk_generic<NMAX, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pk::k_walk_generic<NMAX, A>, block, smem);
+}
+
+template <int NMAX, class A>
+static GenericFns make_fns() {
+    GenericFns f;
+    f.walk = launch_walk_t<NMAX, A>;
+    f.direct = launch_direct_t<NMAX, A>;
+    f.attr = attr_walk_t<NMAX, A>;
+    f.occ = occ_walk_t<NMAX, A>;
+    f.block_log2 = PERM_GENERIC_B;
+    f.devmat_bytes = sizeof(pk::DevMat<NMAX, typename A::V>);
+    return f;
+}
+
+}  // namespace perm
+
+// Defines perm::generic_fns_<NAME>(nmax) for one arithmetic.
+#define PERM_GENERIC_UNIT(NAME, ARITH)                                   \
+    namespace perm {                                                     \
+    GenericFns generic_fns_##NAME(int nmax) {                            \
+        switch (nmax) {                                                  \
+        case 16: return make_fns<16, ARITH>();                           \
+        case 32: return make_fns<32, ARITH>();                           \
+        case 48: return make_fns<48, ARITH>();                           \
+        default: return GenericFns();                                    \
+        }                                                                \
+    }                                                                    \
+    }

@@ -1,0 +1,285 @@
+// host.cpp -- host preprocessing (see host.hpp).
+#include "host.hpp"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+namespace perm {
+
+perm_status_t ingest(const perm_matrix_t *A, Matrix &out, std::string &err) {
+    if (!A) { err = "matrix is NULL"; return PERM_ERR_ARG; }
+    if (A->n < 1 || A->n > kNMax) { err = "n must be in [1, 64]"; return PERM_ERR_SIZE; }
+    if (A->nnz < 0) { err = "nnz < 0"; return PERM_ERR_SIZE; }
+    if (A->layout != PERM_CSR && A->layout != PERM_CSC) { err = "bad layout"; return PERM_ERR_ARG; }
+    if (A->vtype != PERM_F64 && A->vtype != PERM_I64) { err = "bad value type"; return PERM_ERR_ARG; }
+    if (!A->ptr || (A->nnz > 0 && (!A->idx || !A->vals))) { err = "NULL array"; return PERM_ERR_ARG; }
+    const int n = A->n;
+    if (A->ptr[0] != 0 || A->ptr[n] != A->nnz) { err = "ptr[0] must be 0 and ptr[n] must be nnz"; return PERM_ERR_SIZE; }
+    out = Matrix();
+    out.n = n;
+    out.is_int = A->vtype == PERM_I64;
+    if (out.is_int) out.v.assign((size_t)n * n, 0);
+    else out.f.assign((size_t)n * n, 0.0);
+    for (int o = 0; o < n; ++o) {
+        const int b = A->ptr[o], e = A->ptr[o + 1];
+        if (b > e || b < 0 || e > A->nnz) { err = "ptr not monotone"; return PERM_ERR_PATTERN; }
+        int prev = -1;
+        for (int k = b; k < e; ++k) {
+            const int t = A->idx[k];
+            if (t < 0 || t >= n) { err = "index out of range"; return PERM_ERR_PATTERN; }
+            if (t <= prev) { err = "indices not strictly increasing"; return PERM_ERR_PATTERN; }
+            prev = t;
+            const int i = A->layout == PERM_CSR ? o : t;
+            const int j = A->layout == PERM_CSR ? t : o;
+            if (out.is_int) {
+                const int64_t v = ((const int64_t *)A->vals)[k];
+                if (v == 0) continue;
+                out.v[(size_t)i * n + j] = v;
+            } else {
+                const double v = ((const double *)A->vals)[k];
+                if (!std::isfinite(v)) { err = "non-finite value"; return PERM_ERR_ARG; }
+                if (v == 0.0) continue;
+                out.f[(size_t)i * n + j] = v;
+            }
+            out.rowmask[i] |= 1ull << j;
+            out.colmask[j] |= 1ull << i;
+        }
+    }
+    return PERM_OK;
+}
+
+// Kuhn's augmenting paths on the bipartite row/column graph.
+static bool augment(const Matrix &m, int i, uint64_t &seen, int *match_col) {
+    uint64_t cand = m.rowmask[i] & ~seen;
+    while (cand) {
+        const int j = __builtin_ctzll(cand);
+        cand &= cand - 1;
+        seen |= 1ull << j;
+        if (match_col[j] < 0 || augment(m, match_col[j], seen, match_col)) {
+            match_col[j] = i;
+            return true;
+        }
+    }
+    return false;
+}
+
+bool has_perfect_matching(const Matrix &m) {
+    int match_col[kNMax];
+    for (int j = 0; j < m.n; ++j) match_col[j] = -1;
+    for (int i = 0; i < m.n; ++i) {
+        uint64_t seen = 0;
+        if (!augment(m, i, seen, match_col)) return false;
+    }
+    return true;
+}
+
+void order_none(const Matrix &m, int *col_order) {
+    for (int j = 0; j < m.n; ++j) col_order[j] = j;
+}
+
+void order_degree(const Matrix &m, int *col_order) {
+    order_none(m, col_order);
+    std::stable_sort(col_order, col_order + m.n, [&](int a, int b) {
+        return __builtin_popcountll(m.colmask[a]) < __builtin_popcountll(m.colmask[b]);
+    });
+}
+
+// Algorithm 3 (PermanentOrdering).  cdeg[j] counts the nonzeros of column j
+// on rows not yet ordered; each round picks the column with the smallest
+// count (ties: smallest index), orders its unordered rows (in row order, as a
+// CSC scan meets them) and lowers the counts of every column sharing one of
+// those rows.
+void order_alg3(const Matrix &m, int *col_order, int *row_order) {
+    const int n = m.n;
+    const int kInf = INT_MAX / 2;
+    int cdeg[kNMax];
+    bool rmark[kNMax];
+    for (int j = 0; j < n; ++j) cdeg[j] = __builtin_popcountll(m.colmask[j]);
+    for (int i = 0; i < n; ++i) rmark[i] = false;
+    int ridx = 0;
+    for (int cidx = 0; cidx < n; ++cidx) {
+        int col = -1;
+        for (int j = 0; j < n; ++j)
+            if (cdeg[j] < kInf && (col < 0 || cdeg[j] < cdeg[col])) col = j;
+        col_order[cidx] = col;
+        cdeg[col] = kInf;
+        uint64_t rows = m.colmask[col];
+        while (rows) {
+            const int row = __builtin_ctzll(rows);
+            rows &= rows - 1;
+            if (rmark[row]) continue;
+            rmark[row] = true;
+            row_order[ridx++] = row;
+            uint64_t cols = m.rowmask[row];
+            while (cols) {
+                const int c2 = __builtin_ctzll(cols);
+                cols &= cols - 1;
+                if (cdeg[c2] < kInf) cdeg[c2] -= 1;
+            }
+        }
+    }
+    // rows no column reaches (only with an empty row) go last, in index order
+    for (int i = 0; i < n; ++i)
+        if (!rmark[i]) row_order[ridx++] = i;
+}
+
+Layout make_layout(const Matrix &m, const int *col_order, int ordering) {
+    Layout L;
+    const int n = m.n;
+    L.n = n;
+    L.ordering = ordering;
+    for (int p = 0; p < n; ++p) L.col_order[p] = col_order[p];
+    // first touching position of each original row
+    int first[kNMax];
+    for (int i = 0; i < n; ++i) first[i] = n - 1;
+    bool seen[kNMax] = {};
+    int order_seen[kNMax], nseen = 0;
+    for (int p = 0; p < n; ++p) {
+        uint64_t rows = m.colmask[col_order[p]];
+        while (rows) {
+            const int r = __builtin_ctzll(rows);
+            rows &= rows - 1;
+            if (!seen[r]) { seen[r] = true; first[r] = p; order_seen[nseen++] = r; }
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (!seen[i]) order_seen[nseen++] = i;   // empty rows (perm is 0 anyway)
+    // slots: stable by group, inside a group in first-touch order
+    int slot = 0;
+    for (int g = 0; g < n; ++g) {
+        L.group_begin[g] = slot;
+        for (int k = 0; k < n; ++k) {
+            const int r = order_seen[k];
+            if (first[r] == g) { L.row_order[slot] = r; L.slot_of_row[r] = slot; L.group_of_slot[slot] = g; ++slot; }
+        }
+    }
+    L.group_begin[n] = slot;
+    L.top = 0;
+    for (int g = 0; g < n; ++g)
+        if (L.group_begin[g + 1] > L.group_begin[g]) L.top = g;
+    for (int p = 0; p < n; ++p) {
+        uint64_t rows = m.colmask[col_order[p]], mask = 0;
+        while (rows) {
+            const int r = __builtin_ctzll(rows);
+            rows &= rows - 1;
+            mask |= 1ull << L.slot_of_row[r];
+        }
+        L.colmask[p] = mask;
+        L.col_nnz[p] = __builtin_popcountll(mask);
+    }
+    return L;
+}
+
+double cost_per_step(const Layout &L, bool paper_scheme) {
+    const int n = L.n;
+    if (n < 2) return 0.0;
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    double total = 0.0, prefix = 0.0;
+    for (int j = 0; j <= n - 2; ++j) {
+        const double w = std::ldexp(1.0, n - j - 2) / steps;   // Lemma 2
+        prefix += L.group_begin[j + 1] - L.group_begin[j];
+        const double mults = paper_scheme ? (double)(n - 1) : prefix;
+        total += w * (L.col_nnz[j] + mults + 1.0);
+    }
+    return total;
+}
+
+Layout choose_layout(const Matrix &m, int ordering_opt) {
+    int cols[kNMax], rows[kNMax];
+    if (ordering_opt == PERM_ORDER_NONE) { order_none(m, cols); return make_layout(m, cols, PERM_ORDER_NONE); }
+    if (ordering_opt == PERM_ORDER_DEGREE) { order_degree(m, cols); return make_layout(m, cols, PERM_ORDER_DEGREE); }
+    order_alg3(m, cols, rows);
+    Layout paper = make_layout(m, cols, PERM_ORDER_PAPER);
+    if (ordering_opt == PERM_ORDER_PAPER) return paper;
+    order_degree(m, cols);
+    Layout deg = make_layout(m, cols, PERM_ORDER_DEGREE);
+    return cost_per_step(deg, false) < cost_per_step(paper, false) ? deg : paper;
+}
+
+int64_t threads_for_regs(int regs) {
+    int r = std::max(regs, 16);
+    r = (r + 7) / 8 * 8;                       // allocation granularity
+    if (r > 255) return 0;
+    int warps = kRegsPerSM / (r * 32);
+    warps = std::min(warps, kMaxThreadsPerSM / 32);
+    return (int64_t)kSMCount * warps * 32;
+}
+
+// Algorithm 4 (Partitioning), with column n-1 excluded (it never flips) and
+// CalculateNoThreads given by GB300 occupancy at nregisters + base registers.
+void partition_alg4(const Layout &L, double gr_ratio, int base_regs, int *k_out, int *c_out) {
+    const int n = L.n;
+    int k = 0, c = 0, nrows = 0;
+    double best = 0.0;
+    for (int j = 0; j <= n - 2; ++j) {
+        nrows = std::max(nrows, L.group_begin[j + 1]);
+        const int nregisters = nrows * 2;
+        const double w = std::ldexp(1.0, -(j + 1));
+        const double reg_cost = nregisters * (1.0 - w);
+        const double glob_cost = (n - nrows) * w * gr_ratio;
+        const double tau = (double)threads_for_regs(nregisters + base_regs);
+        const double score = tau / (reg_cost + glob_cost);
+        if (score > best || nrows == k) {
+            best = score;
+            k = nrows;
+            c = j + 1;
+        }
+    }
+    if (n < 2) { k = n; c = 0; }
+    *k_out = k;
+    *c_out = c;
+}
+
+double bound_log2(const Matrix &m) {
+    const int n = m.n;
+    bool binary = true;
+    for (int i = 0; i < n && binary; ++i)
+        for (int j = 0; j < n; ++j)
+            if (m.nz(i, j) && !(m.is_int ? m.ival(i, j) == 1 : m.fval(i, j) == 1.0)) { binary = false; break; }
+    double rows = 0.0, cols = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double rs = 0.0, cs = 0.0;
+        for (int j = 0; j < n; ++j) {
+            rs += std::fabs(m.fval(i, j));
+            cs += std::fabs(m.fval(j, i));
+        }
+        if (rs == 0.0 || cs == 0.0) return -INFINITY;
+        if (binary) {
+            rows += std::lgamma(rs + 1.0) / rs / std::log(2.0);   // Bregman-Minc
+            cols += std::lgamma(cs + 1.0) / cs / std::log(2.0);
+        } else {
+            rows += std::log2(rs);
+            cols += std::log2(cs);
+        }
+    }
+    return std::min(rows, cols);
+}
+
+int exact_words_for(double bound, int n) {
+    if (!(bound < 125.0)) return 0;               // result must fit a signed 128-bit integer
+    for (int w = 1; w <= 3; ++w)
+        if (64.0 * w >= bound + n + 2.0) return w; // (n-1) bits of scale, a sign bit, a margin
+    return 0;
+}
+
+std::vector<Launch> alg2_launches(int64_t tau, int n) {
+    std::vector<Launch> out;
+    int64_t start = 1;
+    const int64_t end = (int64_t)1 << (n - 1);
+    while (end - start > 0) {
+        int64_t delta = 1024;
+        while (delta * tau <= end - start) delta *= 2;
+        delta /= 2;
+        if (delta == 512) {
+            out.push_back({start, 1024, end});
+            break;
+        }
+        out.push_back({start, delta, end});
+        start += tau * delta;
+    }
+    return out;
+}
+
+}  // namespace perm

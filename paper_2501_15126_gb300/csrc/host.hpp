@@ -1,0 +1,95 @@
+// host.hpp -- host-side preprocessing of a permanent plan (C++).
+//
+// Ingest (CSR/CSC -> dense, validation), the structural guard (perfect
+// matching), column ordering (degree sort of Sec. VI-B, PermanentOrdering of
+// Algorithm 3), the row grouping behind the product chain, the step-cost
+// model (Lemma 2 weights), Partitioning (Algorithm 4), the a-priori bound that
+// sizes the exact path, and the Gray-code helpers of Sec. IV.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "perm.h"
+
+namespace perm {
+
+constexpr int kNMax = 64;
+constexpr int kBlockLog2 = 5;         // B: 2^B Gray steps unrolled per block
+constexpr int kSMCount = 152;         // GB300
+constexpr int kRegsPerSM = 65536;
+constexpr int kMaxThreadsPerSM = 2048;
+
+struct Matrix {
+    int n = 0;
+    bool is_int = false;
+    std::vector<double> f;    // n*n row-major (FP64 inputs)
+    std::vector<int64_t> v;   // n*n row-major (integer inputs)
+    uint64_t rowmask[kNMax] = {};
+    uint64_t colmask[kNMax] = {};
+    bool nz(int i, int j) const { return (rowmask[i] >> j) & 1ull; }
+    double fval(int i, int j) const { return is_int ? (double)v[(size_t)i * n + j] : f[(size_t)i * n + j]; }
+    int64_t ival(int i, int j) const { return v[(size_t)i * n + j]; }
+};
+
+// Copies and validates a borrowed matrix.  Explicit zeros are dropped.
+perm_status_t ingest(const perm_matrix_t *A, Matrix &out, std::string &err);
+
+// Dense row-major input (internal use by the batch path and tests).
+bool has_perfect_matching(const Matrix &m);
+
+// The plan's ordering of rows and columns.
+struct Layout {
+    int n = 0;
+    int ordering = PERM_ORDER_NONE;
+    int col_order[kNMax] = {};     // position p -> original column
+    int row_order[kNMax] = {};     // slot r -> original row
+    int slot_of_row[kNMax] = {};   // original row -> slot
+    int group_of_slot[kNMax] = {}; // first column position touching the slot's row
+    int group_begin[kNMax + 1] = {};  // slots of group m are [group_begin[m], group_begin[m+1])
+    uint64_t colmask[kNMax] = {};  // by position p: slots touched by that column
+    int col_nnz[kNMax] = {};
+    int top = 0;                   // highest nonempty group
+};
+
+// Column orders.  PAPER is Algorithm 3; its row order is returned too.
+void order_none(const Matrix &m, int *col_order);
+void order_degree(const Matrix &m, int *col_order);
+void order_alg3(const Matrix &m, int *col_order, int *row_order);
+
+// Builds the slot layout for a column order: slots sorted by group, and
+// inside a group in the order the rows were first touched.
+Layout make_layout(const Matrix &m, const int *col_order, int ordering);
+
+// Arithmetic ops per Gray step (Lemma 2 weights 2^(n-j-2)/(2^(n-1)-1)):
+// chain scheme: nnz_j updates + |R_0|+...+|R_j| multiplies + 1 accumulate;
+// paper scheme: nnz_j updates + (n-1) multiplies + 1 accumulate.
+double cost_per_step(const Layout &L, bool paper_scheme);
+
+// Chooses the ordering (AUTO = cheaper of DEGREE and PAPER under the model).
+Layout choose_layout(const Matrix &m, int ordering_opt);
+
+// Algorithm 4 with GB300 occupancy; returns k (register rows) and c.
+void partition_alg4(const Layout &L, double gr_ratio, int base_regs, int *k, int *c);
+
+// GB300 resident threads for a kernel using `regs` registers per thread.
+int64_t threads_for_regs(int regs);
+
+// log2 of an a-priori bound on |perm(A)|: Bregman-Minc for 0/1 matrices,
+// otherwise min over rows/cols of prod of absolute sums.  -inf for zero rows.
+double bound_log2(const Matrix &m);
+
+// Smallest w in 1..3 with the doubled-NW sum recoverable modulo 2^(64 w),
+// or 0 when even w = 3 is not enough.
+int exact_words_for(double bound, int n);
+
+// Theorem 1: column flipped at step i >= 1 and its sign.
+inline int scbs_col(uint64_t i) { return __builtin_ctzll(i); }
+inline int scbs_sign(uint64_t i) { int j = __builtin_ctzll(i); return ((i >> (j + 1)) & 1ull) ? -1 : 1; }
+
+// Algorithm 2 (GenerateLaunchParameters).
+struct Launch { int64_t start, delta, end; };
+std::vector<Launch> alg2_launches(int64_t tau, int n);
+
+}  // namespace perm

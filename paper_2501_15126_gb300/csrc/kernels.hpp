@@ -1,0 +1,36 @@
+// kernels.hpp -- host-side entry points of the precompiled kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "devmat.h"
+
+namespace perm {
+
+// Launchers of one precompiled generic kernel family member.
+struct GenericFns {
+    cudaError_t (*walk)(const pk::BatchArgs &ba, int grid, int block, cudaStream_t st) = nullptr;
+    cudaError_t (*direct)(const void *devmat, uint64_t g_lo, uint64_t g_hi, uint64_t *block_out, int grid, int block,
+                          cudaStream_t st) = nullptr;
+    cudaError_t (*attr)(cudaFuncAttributes *attr) = nullptr;
+    cudaError_t (*occ)(int block, int *blocks_per_sm) = nullptr;
+    int block_log2 = 0;   // B of this family: 2^B steps unrolled per block
+    size_t devmat_bytes = 0;
+};
+
+// arith: 0 = FP64, 1..3 = exact modulo 2^(64 arith).  nmax in {16, 32, 48}.
+GenericFns generic_fns(int nmax, int arith);
+
+// Per-matrix sums of a multi-matrix walk: result[m] = sum of task results
+// [mats[m].task_begin, mats[m+1].task_begin) (the last ends at ntasks), in a
+// fixed order, one warp per matrix.
+cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, uint64_t ntasks,
+                                const uint64_t *task_out, uint64_t *result, cudaStream_t st);
+
+// Sums ntasks task results (words per task: 2 for FP64, arith for exact) in a
+// fixed order into result.
+cudaError_t reduce_launch(int arith, const uint64_t *task_out, uint64_t ntasks, uint64_t *result, cudaStream_t st);
+
+}  // namespace perm

@@ -1,0 +1,63 @@
+// plan.hpp -- the internal state behind a perm_plan_t.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "codegen.hpp"
+#include "host.hpp"
+#include "kernels.hpp"
+
+struct perm_plan_s {
+    perm::Matrix m;
+    perm::Layout L;
+    perm_opts_t opts{};
+    int arith = 0;            // 0 = FP64, 1..3 = exact modulo 2^(64 arith)
+    uint64_t total = 0;       // 2^(n-1)
+    uint64_t g_lo = 0, g_hi = 0;
+    bool subrange = false;
+    bool zero = false;        // no perfect matching: perm is 0, nothing launches
+    bool direct = false;      // tiny n: one thread per Gray index
+    double bound = 0.0;
+    double ops_per_step = 0.0, ops_per_step_paper = 0.0;
+    double ms_plan = 0.0, ms_compile = 0.0;
+    int engine = 0, nmax = 0, words = 2;
+    int K = 0, grid = 1, block = 256, regs = 0;
+    int k = 0, c = 0;         // Algorithm 4 split (codegen)
+    uint64_t chunk_lo = 0, chunk_hi = 0, ntasks = 0;
+    perm::GenericFns gf;
+    perm::CodegenKernel cg;
+    void *d_devmat = nullptr;
+    uint64_t *d_ws = nullptr;   // [0] task counter, [1] skipped blocks, [2..4] result, [8..] task results
+    void *d_xglob = nullptr;    // codegen: rows of x kept in global memory
+    uint64_t *h_res = nullptr;  // pinned copy of d_ws[0..7]
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    uint64_t len() const { return g_hi - g_lo; }
+    ~perm_plan_s();
+};
+
+namespace perm {
+
+// Workspace layout (64-bit words): [0] task counter, [1] skipped blocks,
+// [2..4] reduced result, [8..12] the single-matrix BatchMat, [16..] task results.
+constexpr size_t kWsBatchMat = 8;
+constexpr size_t kWsTaskOut = 16;
+
+perm_status_t fail(perm_status_t s, const std::string &msg);
+perm_status_t cuda_fail(cudaError_t e, const char *what);
+double now_ms();
+
+// Stages of perm_plan_create / perm_compute, reused by batch and serving.
+perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_s &P);
+perm_status_t plan_device_setup(perm_plan_s &P);
+perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st);
+perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out);
+void describe(const perm_plan_s &P, perm_result_t *out);
+perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);
+int nmax_bucket(int n);
+void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img);
+
+}  // namespace perm

@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs.  Exact (integer) results must be bit-identical; FP64
+results must agree within 1e-9 relative to |perm| (the tolerance of the FP64
+path), and sub-range partial sums within 1e-9 of the range's sum of |terms|."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_15126_gb300 import _abi as A
+from paper_2501_15126_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+MASK128 = (1 << 128) - 1
+RTOL = 1e-9
+
+
+def rel_err(got, want):
+    return abs(got - want) / max(abs(want), 1e-300)
+
+
+def fp_ok(res, a, threads=8):
+    want, absum = oracle.nw_perm(a, threads=threads)
+    err = abs(res.value - float(want))
+    return err <= RTOL * abs(float(want)), err / max(abs(float(want)), 1e-300)
+
+
+def rand_pattern(n, p, seed, values):
+    g = np.random.default_rng(seed)
+    pat = g.random((n, n)) < p
+    np.fill_diagonal(pat, True)
+    if values == "int":
+        return (g.integers(-3, 4, size=(n, n)) * pat).astype(np.int64)
+    if values == "01":
+        return pat.astype(np.int64)
+    return g.random((n, n)) * pat
+
+
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9, 12, 15, 19])
+def test_small_n_exact_matches_oracle(n, engine):
+    if engine == A.PERM_ENGINE_CODEGEN and n <= 8:
+        pytest.skip("n <= 8 runs the direct kernel")
+    for seed, vals in ((n, "01"), (100 + n, "int")):
+        a = rand_pattern(n, 0.4, seed, vals)
+        want = oracle.ryser_gray(a)
+        r = A.permanent(a, engine=engine)
+        assert r.status == 0 and r.value == want, (n, vals, r.value, want)
+
+
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 9, 13, 17, 20])
+def test_small_n_f64_matches_oracle(n, engine):
+    if engine == A.PERM_ENGINE_CODEGEN and n <= 8:
+        pytest.skip("n <= 8 runs the direct kernel")
+    a = rand_pattern(n, 0.5, 7 * n, "f64")
+    if n <= 9:
+        want = float(oracle.brute(a))
+    else:
+        want = float(oracle.nw_perm(a, threads=8)[0])
+    r = A.permanent(a, engine=engine)
+    assert rel_err(r.value, want) <= RTOL, (n, r.value, want)
+
+
+def test_cfg1_exact_and_f64():
+    """n=24, ER p=0.2 + diagonal, 0/1 values: bit-exact; the same pattern with
+    (0,1] values: FP64 within 1e-9."""
+    a01 = synth.single_er(24, 0.2, 1, values="01")
+    want = oracle.ryser_gray(a01)
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        r = A.permanent(a01, engine=engine)
+        assert r.value == want
+    pi, pf = synth.single_er_pair(24, 0.2, 1)
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        ok, err = fp_ok(A.permanent(pf, engine=engine), pf)
+        assert ok, err
+
+
+def test_orderings_engines_and_words_agree_exactly():
+    a = synth.single_er(22, 0.25, 9, values="01")
+    want = oracle.ryser_gray(a)
+    for ordering in (A.PERM_ORDER_NONE, A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER, A.PERM_ORDER_AUTO):
+        for words in (0, 2, 3):
+            for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+                r = A.permanent(a, ordering=ordering, exact_words=words, engine=engine)
+                assert r.value == want, (ordering, words, engine)
+
+
+def test_zero_skip_and_chunking_do_not_change_exact_results():
+    a = synth.band_plus(n=26, w=2, extra=1, seed=5, values="01")
+    want = oracle.ryser_gray(a)
+    for zs in (0, 1):
+        for K in (0, 8, 12):
+            for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+                r = A.permanent(a, zero_skip=zs, chunk_log2=K, engine=engine)
+                assert r.value == want
+
+
+def test_codegen_register_global_split():
+    """Rows beyond k live in global memory (Algorithm 4 split); any k gives the same value."""
+    a = synth.single_er(21, 0.2, 11, values="01")
+    want = oracle.ryser_gray(a)
+    af = synth.single_er(21, 0.2, 11, values="f64")
+    wantf = float(oracle.nw_perm(af, threads=8)[0])
+    for k in (0, 1, 6, 10, 14, 21):
+        r = A.permanent(a, engine=A.PERM_ENGINE_CODEGEN, reg_rows=k)
+        assert r.value == want, k
+        rf = A.permanent(af, engine=A.PERM_ENGINE_CODEGEN, reg_rows=k)
+        assert rel_err(rf.value, wantf) <= RTOL, k
+
+
+def test_structurally_zero_and_edge_cases():
+    a = np.eye(6, dtype=np.int64)
+    a[2, 2] = 0
+    assert A.permanent(a).value == 0                       # empty row
+    b = np.zeros((5, 5), dtype=np.int64)
+    b[:, 0] = 1
+    b[0, :] = 1
+    assert A.permanent(b).value == 0                       # no perfect matching
+    assert A.permanent(np.array([[7]], dtype=np.int64)).value == 7
+    assert A.permanent(np.array([[-2.5]])).value == -2.5
+    n = 20
+    assert A.permanent(synth.ones(n)).value == math.factorial(n)
+    assert A.permanent(synth.permutation_matrix(30, 3)).value == 1
+
+
+def test_exact_negative_entries():
+    a = rand_pattern(18, 0.35, 4, "int")
+    assert A.permanent(a).value == oracle.ryser_gray(a)
+
+
+def test_deterministic_repeat():
+    a = synth.single_er(28, 0.2, 12, values="f64")
+    p = A.Plan(a)
+    r1, r2 = p.compute(), p.compute()
+    assert (r1.f64, r1.f64_lo) == (r2.f64, r2.f64_lo)
+    p.close()
+
+
+# ------------------------------------------------------------------ sub-ranges at full size
+
+def in_plan_order(a, **kw):
+    """A partial sum over a Gray sub-range depends on the column order (the
+    walk visits subsets of the ordered columns, and the last ordered column is
+    the one never flipped), so the oracle gets the columns in the plan's order."""
+    ins = A.inspect(a, ordering=kw.get("ordering", 0))
+    order = list(ins.col_order)[: a.shape[0]]
+    return np.ascontiguousarray(a[:, order])
+
+
+def subrange_check_f64(a, lo, hi, **kw):
+    r = A.permanent(a, g_lo=lo, g_hi=hi, **kw)
+    s, sa = oracle.nw_range(in_plan_order(a, **kw), lo, hi, threads=16)
+    assert abs(r.value - float(s)) <= RTOL * float(sa), (lo, hi, r.value, float(s), float(sa))
+
+
+def subrange_check_exact(a, lo, hi, **kw):
+    r = A.permanent(a, g_lo=lo, g_hi=hi, **kw)
+    want = oracle.nw2_range(in_plan_order(a, **kw), lo, hi, threads=16)
+    assert r.partial_int & MASK128 == want, (lo, hi)
+
+
+def test_subrange_sums_add_up_to_the_permanent():
+    """Partial sums over a split of [0, 2^(n-1)) add up to the full walk."""
+    a = synth.single_er(22, 0.3, 21, values="01")
+    want = oracle.ryser_gray(a)
+    n = 22
+    cuts = [0, 1 << 10, 3 << 15, 1 << 20, 1 << 21]
+    tot = sum(A.permanent(a, g_lo=lo, g_hi=hi).partial_int for lo, hi in zip(cuts, cuts[1:]))
+    r = A.permanent(a)
+    w = r.exact_words
+    assert tot % (1 << (64 * w)) == ((-1) ** (n - 1) * (1 << (n - 1)) * want) % (1 << (64 * w))
+    af = synth.single_er(22, 0.3, 21, values="f64")
+    parts = sum(A.permanent(af, g_lo=lo, g_hi=hi).value for lo, hi in zip(cuts, cuts[1:]))
+    assert rel_err(-2.0 * parts, A.permanent(af).value) < 1e-12
+
+
+def test_cfg2_subranges():
+    """n=36, ER p=0.15 + diagonal, (0,1] values, shuffled columns: Gray sub-ranges
+    anywhere in [0, 2^35), including ranges whose high bits are set."""
+    a = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
+    span = 1 << 20
+    for lo in (0, 1 << 25, (1 << 34) + (3 << 27), (1 << 35) - span):
+        for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+            subrange_check_f64(a, lo, lo + span, engine=engine)
+
+
+def test_cfg3_subranges_exact_and_f64():
+    """n=48 band |i-j|<=3 + 2 off-band nonzeros per row, with the register/global split."""
+    a01 = synth.band_plus(48, 3, 2, seed=3, values="01")
+    af = synth.band_plus(48, 3, 2, seed=3, values="f64")
+    span = 1 << 20
+    for lo in (0, 1 << 30, (1 << 46) + (5 << 33), (1 << 47) - span):
+        subrange_check_exact(a01, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN)
+        subrange_check_f64(af, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN)
+        subrange_check_exact(a01, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN, reg_rows=20)
+        subrange_check_f64(af, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN, reg_rows=20)
+    subrange_check_exact(a01, 1 << 30, (1 << 30) + span, engine=A.PERM_ENGINE_GENERIC)
