@@ -31,6 +31,8 @@ import tempfile
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -218,9 +220,8 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_2501_15126_gb300 import dist as pd
+        total_ms = pd.max_over_ranks(total_ms, device=dev)
         torch.distributed.barrier()
 
     # end to end through the public API from host memory, every step
@@ -275,6 +276,146 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The 10,000-matrix workload: one persistent launch per kernel family
+    (perm_batch) against one plan and launch per matrix (perm_batch_sequential)."""
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    from paper_2501_15126_gb300 import synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    items = synth.batch(count=args.batch_count)
+    mats = [A.CSRMatrix(it.a) for it in items]
+    steps_total = sum(1 << (it.n - 1) for it in items)
+    for _ in range(max(args.warmup, 1)):
+        A.batch(mats, stream=stream.cuda_stream)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = A.batch(mats, stream=stream.cuda_stream)
+        times.append(time.perf_counter() - t0)
+    seq_t0 = time.perf_counter()
+    seq = A.batch(mats, sequential=True, stream=stream.cuda_stream)
+    seq_time = time.perf_counter() - seq_t0
+    mism_exact = sum(1 for r, q, it in zip(res, seq, items) if it.values == "01" and r.value != q.value)
+    mism_f64 = sum(1 for r, q, it in zip(res, seq, items)
+                   if it.values == "f64" and abs(r.value - q.value) > 1e-9 * abs(q.value))
+    max_rel_f64 = max((abs(r.value - q.value) / abs(q.value) for r, q, it in zip(res, seq, items)
+                       if it.values == "f64"), default=0.0)
+    best = min(times)
+    line = {"metric": "batched permanents/s (10,000 matrices, n in [12,28])", "value": len(items) / best,
+            "unit": "perms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * best, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+exact", "data": "synthetic",
+            "config": {"workload": "batch of %d ER matrices, n uniform in [12,28], p uniform in [0.2,0.4] + forced "
+                                   "diagonal, alternating 0/1 (exact) and (0,1] (FP64), seed 4" % len(items),
+                       "gray_steps_total": steps_total, "l2": "inputs re-uploaded every step"},
+            "gray_steps_per_s": steps_total / best,
+            "sequential": {"seconds": seq_time, "perms_per_s": len(items) / seq_time,
+                           "note": "perm_batch_sequential: plan + launch + sync + destroy per matrix"},
+            "speedup_vs_sequential": seq_time / best,
+            "agreement_vs_sequential": {"exact_mismatches": mism_exact, "f64_beyond_1e-9": mism_f64,
+                                        "f64_max_rel_diff": max_rel_f64},
+            "kernel_ms": res[0].ms_kernel}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Open-loop replay of the Poisson serving stream against the server, and
+    the same arrivals served by one plan + launch per request in order."""
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    from paper_2501_15126_gb300 import synth
+    torch.cuda.set_device(0)
+    reqs = synth.serving_stream(rate=args.rate, duration=args.duration, seed=5)
+    mats = [A.CSRMatrix(r.a) for r in reqs]
+    arrivals = [r.t_arrival for r in reqs]
+
+    def replay_server():
+        lat = [None] * len(reqs)
+        res = [None] * len(reqs)
+        with A.Server() as s:
+            # warm the families up
+            for m in mats[:50]:
+                s.poll(s.submit(m), 60000)
+            tickets = [None] * len(reqs)
+            done_evt = threading.Event()
+
+            def collector():
+                for i in range(len(reqs)):
+                    while tickets[i] is None:
+                        time.sleep(0.0001)
+                    r = s.poll(tickets[i], -1)
+                    lat[i] = time.perf_counter() - (t0 + arrivals[i])
+                    res[i] = r
+                done_evt.set()
+            t0 = time.perf_counter()
+            th = threading.Thread(target=collector)
+            th.start()
+            for i, m in enumerate(mats):
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = s.submit(m)
+            th.join()
+            wall = time.perf_counter() - t0
+        return lat, res, wall
+
+    def replay_sequential():
+        lat = [None] * len(reqs)
+        res = [None] * len(reqs)
+        t0 = time.perf_counter()
+        for i, m in enumerate(mats):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            res[i] = A.permanent(m)
+            lat[i] = time.perf_counter() - (t0 + arrivals[i])
+        return lat, res, time.perf_counter() - t0
+
+    ls, rs, ws = replay_server()
+    lq, rq, wq = replay_sequential()
+    q = lambda v, p: float(np.percentile(np.array(v) * 1e3, p))
+    bad = [(i, reqs[i].a.shape[0], reqs[i].values, a.status, a.value, b.value) for i, (a, b) in enumerate(zip(rs, rq))
+           if a.status or b.status or (a.value != b.value if a.vtype == 1 else abs(a.value - b.value) > 1e-9 * abs(b.value))]
+    mism = len(bad)
+    line = {"metric": "served permanents/s with p50/p99 latency (Poisson 2,000 req/s)",
+            "value": len(reqs) / ws, "unit": "perms/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+exact", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals at %g req/s for %g s (%d requests), n = 16 + m with P(m) ~ 2^-m "
+                                   "up to 40, p uniform in [0.1,0.3] + diagonal, mixed 0/1 and (0,1], seed 5"
+                                   % (args.rate, args.duration, len(reqs))},
+            "p50_ms": q(ls, 50), "p99_ms": q(ls, 99), "max_ms": q(ls, 100),
+            "sequential": {"perms_per_s": len(reqs) / wq, "p50_ms": q(lq, 50), "p99_ms": q(lq, 99),
+                           "max_ms": q(lq, 100)},
+            "mismatches_vs_sequential": mism, "mismatch_examples": [list(map(str, b)) for b in bad[:5]]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_profile_case(args):
+    """A small case of the bench kernel for `ncu --set full`: the same matrix,
+    plan and generated kernel, walking only the Gray sub-range [0, 2^k)."""
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    torch.cuda.set_device(0)
+    a = workload_matrix()
+    vals = "01" if args.profile_exact else "f64"
+    if args.profile_exact:
+        from paper_2501_15126_gb300 import synth
+        a = synth.band_plus(48, 3, 2, seed=3, values="01")
+    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2)
+    for _ in range(args.steps):
+        r = p.compute()
+    print(json.dumps({"profile_case": vals, "gray_steps": r.steps, "ms_kernel": r.ms_kernel,
+                      "ops_per_step": r.fp_ops_per_step, "threads": r.threads, "regs": r.regs_per_thread,
+                      "chunk_log2": r.chunk_log2, "zero_skip_frac": r.zero_skip_frac}))
+    p.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,11 +424,23 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile"])
+    ap.add_argument("--profile-log2", type=int, default=30)
+    ap.add_argument("--profile-exact", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=10_000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--duration", type=float, default=60.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload == "profile":
+        return run_profile_case(args)
     return run_ours(args)
 
 

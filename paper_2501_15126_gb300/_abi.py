@@ -241,6 +241,56 @@ def issue_rates(stream: int = 0):
     return f.value, i.value
 
 
+class Server:
+    """perm_server_create / perm_submit / perm_poll / perm_server_destroy."""
+
+    def __init__(self, max_inflight=0, max_n=0, step_budget=0.0, device=0, timeout_ms=0):
+        o = ServerOpts(max_inflight, max_n, step_budget, device, timeout_ms)
+        h = c_vp()
+        check(lib().perm_server_create(ctypes.byref(o), ctypes.byref(h)), "perm_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, a) -> int:
+        m = a if isinstance(a, CSRMatrix) else CSRMatrix(a)
+        t = c_u64()
+        st = lib().perm_submit(self.h, ctypes.byref(m.c), ctypes.byref(t))
+        check(st, "perm_submit")
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Result, or None when not ready within timeout_ms."""
+        r = Result()
+        st = lib().perm_poll(self.h, ticket, timeout_ms, ctypes.byref(r))
+        if st == PERM_ERR_NOT_READY:
+            return None
+        check(st, "perm_poll")
+        return r
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        check(lib().perm_server_stats(self.h, ctypes.byref(s)), "perm_server_stats")
+        return s
+
+    def close(self):
+        if self.h:
+            lib().perm_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch(mats, sequential: bool = False, stream: int = 0, **kw):
     ms = [m if isinstance(m, CSRMatrix) else CSRMatrix(m) for m in mats]
     arr = (Matrix * len(ms))(*[m.c for m in ms])

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,15 +19,24 @@
 
 namespace perm {
 
-static thread_local std::string g_last_error;
+// The last error message of the calling thread: a fixed buffer, so that
+// reporting an error never allocates.
+static thread_local char g_last_error[512];
 
-perm_status_t fail(perm_status_t s, const std::string &msg) {
-    g_last_error = msg;
+static void set_error(const char *a, const char *b) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s%s%s", a ? a : "", (a && b) ? ": " : "", b ? b : "");
+}
+
+perm_status_t fail(perm_status_t s, const char *msg) {
+    set_error(msg, nullptr);
     return s;
 }
 
+perm_status_t fail(perm_status_t s, const std::string &msg) { return fail(s, msg.c_str()); }
+
 perm_status_t cuda_fail(cudaError_t e, const char *what) {
-    return fail(PERM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    set_error(what, cudaGetErrorString(e));
+    return PERM_ERR_CUDA;
 }
 
 double now_ms() {
@@ -44,21 +54,32 @@ int nmax_bucket(int n) {
 static int floor_log2(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
 
 // Builds the shared-memory image read by the generic kernels.
+size_t devmat_bytes(int arith, int nmax) {
+    const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
+    return 16 + 8 * (size_t)nmax * 2 + vsz * (size_t)nmax * (1 + (size_t)nmax);
+}
+
 void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img) {
+    img.assign(devmat_bytes(arith, nmax), 0);
+    build_devmat_into(m, L, arith, nmax, img.data());
+}
+
+void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, unsigned char *dst) {
     const int n = m.n;
     const int last = L.col_order[n - 1];
     const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
     const size_t head = 16 + 8 * (size_t)nmax * 2;
-    img.assign(head + vsz * (size_t)nmax * (1 + (size_t)nmax), 0);
-    int32_t *hdr = reinterpret_cast<int32_t *>(img.data());
+    std::memset(dst, 0, devmat_bytes(arith, nmax));
+    unsigned char *base = dst;
+    int32_t *hdr = reinterpret_cast<int32_t *>(base);
     hdr[0] = n;
     hdr[1] = L.top;
-    uint64_t *colmask = reinterpret_cast<uint64_t *>(img.data() + 16);
+    uint64_t *colmask = reinterpret_cast<uint64_t *>(base + 16);
     uint64_t *grpmask = colmask + nmax;
     for (int p = 0; p + 1 < n; ++p) colmask[p] = L.colmask[p];
     for (int g = 0; g < n; ++g)
         for (int s = L.group_begin[g]; s < L.group_begin[g + 1]; ++s) grpmask[g] |= 1ull << s;
-    unsigned char *x0 = img.data() + head;
+    unsigned char *x0 = base + head;
     unsigned char *val = x0 + vsz * nmax;
     for (int s = 0; s < n; ++s) {
         const int r = L.row_order[s];
@@ -100,13 +121,14 @@ static bool exact_fits_int32(const Matrix &m) {
     return true;
 }
 
-perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, perm_plan_s &P) {
+perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, perm_plan_s &P, void *storage,
+                           size_t storage_bytes) {
     const double t0 = now_ms();
     perm_opts_t opts;
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
-    std::string err;
-    perm_status_t st = ingest(A, P.m, err);
+    const char *err = nullptr;
+    perm_status_t st = ingest(A, P.m, &err, storage, storage_bytes);
     if (st != PERM_OK) return fail(st, err);
     const int n = P.m.n;
     P.opts = opts;
@@ -150,7 +172,7 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
 }
 
 // Chooses K, grid and block for a walk over [g_lo, g_hi).
-static perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block) {
+perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block) {
     const uint64_t len = P.g_hi - P.g_lo;
     const int n = P.m.n;
     int kmax = n - 1;
@@ -160,10 +182,11 @@ static perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_pe
     const int64_t resident_warps = (int64_t)kSMCount * blocks_per_sm * (block / 32);
     int K = P.opts.chunk_log2;
     if (!K) {
-        // enough 32-chunk tasks for every resident warp several times over
+        // enough 32-chunk tasks for every resident warp several times over, but
+        // chunks of at least 2^(B+3) steps so the start vector stays a small cost
         const double want_tasks = 8.0 * (double)resident_warps;
         K = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * want_tasks)));
-        K = std::max(K, block_log2 + 8);   // amortise the start vector over >= 2^(B+8) steps
+        K = std::max(K, block_log2 + 3);
     }
     K = std::min(K, kmax);
     if (K < block_log2) return fail(PERM_ERR_ARG, "range too short or misaligned for the chunk size");
@@ -262,6 +285,8 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
         pk::BatchMat bm;
         std::memset(&bm, 0, sizeof(bm));
         bm.task_begin = 0;
+        bm.out_offset = 0;
+        bm.image = 0;
         bm.chunk_lo = P.chunk_lo;
         bm.chunk_hi = P.chunk_hi;
         bm.K = P.K;
@@ -446,8 +471,8 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     std::memset(&opts, 0, sizeof(opts));
     if (opts_in) opts = *opts_in;
     Matrix m;
-    std::string err;
-    perm_status_t st = ingest(A, m, err);
+    const char *err = nullptr;
+    perm_status_t st = ingest(A, m, &err);
     if (st != PERM_OK) return fail(st, err);
     if (opts.ordering < 0 || opts.ordering > PERM_ORDER_PAPER) return fail(PERM_ERR_ARG, "bad ordering");
     const Layout L = choose_layout(m, opts.ordering);
@@ -533,7 +558,7 @@ const char *perm_status_string(perm_status_t s) {
     return "unknown status";
 }
 
-const char *perm_last_error(void) { return g_last_error.c_str(); }
+const char *perm_last_error(void) { return g_last_error; }
 
 int32_t perm_device_available(void) {
     int count = 0;

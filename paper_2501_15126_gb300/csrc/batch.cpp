@@ -59,6 +59,8 @@ int BatchGroup::setup(int nmax_, int arith_, int K_target) {
         mats[i].task_begin = ntasks;
         mats[i].chunk_lo = 0;
         mats[i].chunk_hi = P.chunk_hi;
+        mats[i].out_offset = ntasks;
+        mats[i].image = (int)i;
         mats[i].K = K;
         ntasks += P.ntasks;
     }

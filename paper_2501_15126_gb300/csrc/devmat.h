@@ -18,14 +18,19 @@ struct WalkArgs {
     int zero_skip;                      // 1 = skip all-zero blocks
 };
 
-// One matrix of a generic (multi-matrix) walk: its tasks are
-// [task_begin, task_begin + ceil((chunk_hi - chunk_lo) / 32)).
+// One entry of a generic (multi-matrix) walk: the launch's tasks
+// [task_begin, next entry's task_begin) walk chunks chunk_lo + 32 t + lane
+// (t counted from task_begin) of the matrix image `image`, and task t's
+// result goes to task_out[(out_offset + t - task_begin) * words].  A batch
+// has out_offset == task_begin; the serving loop points several launches'
+// slices of one request at that request's own result range.
 struct BatchMat {
     unsigned long long task_begin;
     unsigned long long chunk_lo;
     unsigned long long chunk_hi;
+    unsigned long long out_offset;
+    int image;
     int K;
-    int pad;
 };
 
 // Launch arguments of the generic kernels: any number of matrices of one

@@ -28,9 +28,41 @@ __global__ void __launch_bounds__(256) k_batch_reduce(const BatchMat *mats, int 
     if (lane == 0) A::acc_store(result + (u64)m * A::ACC_WORDS, acc);
 }
 
+// Serving: segment m sums pool[seg[2m] .. seg[2m] + seg[2m+1]) (task units),
+// one warp per segment, fixed order.
+template <class A>
+__global__ void __launch_bounds__(256) k_segment_reduce(const u64 *seg, int nseg, const u64 *pool, u64 *result) {
+    const int m = (int)((blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (m >= nseg) return;
+    const u64 b = seg[2 * m], e = b + seg[2 * m + 1];
+    typename A::Acc acc = A::acc_zero();
+    for (u64 t = b + lane; t < e; t += 32) acc = A::acc_add(acc, A::acc_load(pool + t * (u64)A::ACC_WORDS));
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
+    if (lane == 0) A::acc_store(result + (u64)m * 4, acc);
+}
+
 }  // namespace pk
 
 namespace perm {
+
+cudaError_t segment_reduce_launch(int arith, const uint64_t *seg, int nseg, const uint64_t *pool, uint64_t *result,
+                                  cudaStream_t st) {
+    const unsigned long long *sg = reinterpret_cast<const unsigned long long *>(seg);
+    const unsigned long long *in = reinterpret_cast<const unsigned long long *>(pool);
+    unsigned long long *out = reinterpret_cast<unsigned long long *>(result);
+    const int grid = (nseg * 32 + 255) / 256;
+    if (nseg <= 0) return cudaSuccess;
+    switch (arith) {
+    case 0: pk::k_segment_reduce<pk::ArithF64><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 1: pk::k_segment_reduce<pk::ArithExact<1>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 2: pk::k_segment_reduce<pk::ArithExact<2>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 3: pk::k_segment_reduce<pk::ArithExact<3>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, uint64_t ntasks,
                                 const uint64_t *task_out, uint64_t *result, cudaStream_t st) {

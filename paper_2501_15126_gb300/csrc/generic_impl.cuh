@@ -22,6 +22,21 @@
 
 namespace pk {
 
+// Register-slot access by a run-time index: a switch whose cases name x[k]
+// with a compile-time k, so x stays in registers.  The switch argument is
+// warp-uniform (a bit of a column or group mask), so it is a uniform jump,
+// and only the slots a column really touches cost an arithmetic instruction.
+// Each data-driven loop ends in __syncwarp(): the compiler cannot prove the
+// masks uniform, and without an explicit reconvergence point the warp's
+// lanes can drift apart and run the loops one path at a time.
+// (A predicated loop over all NMAX slots would issue NMAX FP64 instructions
+// per flip whatever the mask: on GB300, where FP64 issues at 1/64 of FP32,
+// that dominates everything else.)
+#define PERM_SLOT_CASES(F)                                                                              \
+    F(0) F(1) F(2) F(3) F(4) F(5) F(6) F(7) F(8) F(9) F(10) F(11) F(12) F(13) F(14) F(15) F(16) F(17)   \
+    F(18) F(19) F(20) F(21) F(22) F(23) F(24) F(25) F(26) F(27) F(28) F(29) F(30) F(31) F(32) F(33)     \
+    F(34) F(35) F(36) F(37) F(38) F(39) F(40) F(41) F(42) F(43) F(44) F(45) F(46) F(47)
+
 template <int NMAX, class A>
 struct GenericPol {
     static constexpr int NX = NMAX;
@@ -36,48 +51,82 @@ struct GenericPol {
 
     __device__ __forceinline__ explicit GenericPol(const M *mat) : m(mat) {}
 
+    // x[i] = x[i] + s * v for a run-time slot i
+    __device__ __forceinline__ static void add_slot(X (&x)[NX], int i, V v, int s) {
+        switch (i) {
+#define PERM_ADD_CASE(k)                                              \
+    case k:                                                           \
+        if constexpr (k < NMAX) x[k] = A::upd_rt(x[k], v, s);         \
+        break;
+            PERM_SLOT_CASES(PERM_ADD_CASE)
+#undef PERM_ADD_CASE
+        default: break;
+        }
+    }
+    template <int S>
+    __device__ __forceinline__ static void add_slot_s(X (&x)[NX], int i, V v) {
+        switch (i) {
+#define PERM_ADDS_CASE(k)                                             \
+    case k:                                                           \
+        if constexpr (k < NMAX) x[k] = A::template upd<S>(x[k], v);   \
+        break;
+            PERM_SLOT_CASES(PERM_ADDS_CASE)
+#undef PERM_ADDS_CASE
+        default: break;
+        }
+    }
+    __device__ __forceinline__ static X get_slot(const X (&x)[NX], int i) {
+        switch (i) {
+#define PERM_GET_CASE(k)                                              \
+    case k:                                                           \
+        if constexpr (k < NMAX) return x[k];                          \
+        break;
+            PERM_SLOT_CASES(PERM_GET_CASE)
+#undef PERM_GET_CASE
+        default: break;
+        }
+        return x[0];
+    }
+
     template <int J, int S>
     __device__ __forceinline__ void flip(X (&x)[NX]) {
-        const u64 cm = ((const volatile u64 *)m->colmask)[J];
+        u64 cm = ((const volatile u64 *)m->colmask)[J];
         const volatile V *v = m->val + J * NMAX;
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-            if ((cm >> i) & 1ull) x[i] = A::template upd<S>(x[i], v[i]);
+        while (cm) {
+            const int i = ctz64(cm);
+            cm &= cm - 1;
+            add_slot_s<S>(x, i, v[i]);
+        }
+        __syncwarp();
     }
     template <int J>
-    __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) {
-        const u64 cm = ((const volatile u64 *)m->colmask)[J];
-        const volatile V *v = m->val + J * NMAX;
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-            if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], v[i], s);
-    }
+    __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
     __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {
-        const u64 cm = ((const volatile u64 *)m->colmask)[j];
+        u64 cm = ((const volatile u64 *)m->colmask)[j];
         const volatile V *v = m->val + j * NMAX;
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-            if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], v[i], s);
-    }
-    template <int G>
-    __device__ __forceinline__ P grp(const X (&x)[NX], P q) const {
-        const u64 gm = ((const volatile u64 *)m->grpmask)[G];
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-            if ((gm >> i) & 1ull) q = A::mul(q, x[i]);
-        return q;
+        while (cm) {
+            const int i = ctz64(cm);
+            cm &= cm - 1;
+            add_slot(x, i, v[i], s);
+        }
+        __syncwarp();
     }
     __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
-        const u64 gm = ((const volatile u64 *)m->grpmask)[g];
-#pragma unroll
-        for (int i = 0; i < NMAX; ++i)
-            if ((gm >> i) & 1ull) q = A::mul(q, x[i]);
+        u64 gm = ((const volatile u64 *)m->grpmask)[g];
+        while (gm) {
+            const int i = ctz64(gm);
+            gm &= gm - 1;
+            q = A::mul(q, get_slot(x, i));
+        }
+        __syncwarp();
         return q;
     }
+    template <int G>
+    __device__ __forceinline__ P grp(const X (&x)[NX], P q) const { return grp_dyn(G, x, q); }
     // x = x0 + sum of the columns set in Gray code G (columns < n-1 only)
     __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
 #pragma unroll
-        for (int i = 0; i < NMAX; ++i) x[i] = m->x0[i];
+        for (int i = 0; i < NMAX; ++i) x[i] = ((const volatile V *)m->x0)[i];
         while (G) {
             const int p = ctz64(G);
             G &= G - 1;
@@ -134,16 +183,16 @@ __global__ void __launch_bounds__(256) k_walk_generic(BatchArgs ba) {
             m = lo;
         }
         m = __shfl_sync(PERM_FULLMASK, m, 0);
-        if (m != cached) {
+        const BatchMat bm = ba.mats[m];
+        if (bm.image != cached) {
             __syncwarp();
             const uint4 *src = reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const unsigned char *>(ba.devmats) + (size_t)m * ba.devmat_stride);
+                reinterpret_cast<const unsigned char *>(ba.devmats) + (size_t)bm.image * ba.devmat_stride);
             uint4 *dst = reinterpret_cast<uint4 *>(slot);
             for (int i = lane; i < (int)(sizeof(M) / 16); i += 32) dst[i] = src[i];
             __syncwarp();
-            cached = m;
+            cached = bm.image;
         }
-        const BatchMat bm = ba.mats[m];
         u64 q = bm.chunk_lo + (task - bm.task_begin) * 32ull + (u64)lane;
         const bool live = q < bm.chunk_hi;
         if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
@@ -152,7 +201,7 @@ __global__ void __launch_bounds__(256) k_walk_generic(BatchArgs ba) {
         if (!live) acc = A::acc_zero();
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
-        if (lane == 0) A::acc_store(ba.task_out + task * (u64)A::ACC_WORDS, acc);
+        if (lane == 0) A::acc_store(ba.task_out + (bm.out_offset + (task - bm.task_begin)) * (u64)A::ACC_WORDS, acc);
     }
     if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
 }

@@ -8,7 +8,9 @@
 
 namespace perm {
 
-perm_status_t ingest(const perm_matrix_t *A, Matrix &out, std::string &err) {
+perm_status_t ingest(const perm_matrix_t *A, Matrix &out, const char **errp, void *storage, size_t storage_bytes) {
+    const char *dummy = nullptr;
+    const char *&err = errp ? *errp : dummy;
     if (!A) { err = "matrix is NULL"; return PERM_ERR_ARG; }
     if (A->n < 1 || A->n > kNMax) { err = "n must be in [1, 64]"; return PERM_ERR_SIZE; }
     if (A->nnz < 0) { err = "nnz < 0"; return PERM_ERR_SIZE; }
@@ -17,11 +19,21 @@ perm_status_t ingest(const perm_matrix_t *A, Matrix &out, std::string &err) {
     if (!A->ptr || (A->nnz > 0 && (!A->idx || !A->vals))) { err = "NULL array"; return PERM_ERR_ARG; }
     const int n = A->n;
     if (A->ptr[0] != 0 || A->ptr[n] != A->nnz) { err = "ptr[0] must be 0 and ptr[n] must be nnz"; return PERM_ERR_SIZE; }
-    out = Matrix();
     out.n = n;
     out.is_int = A->vtype == PERM_I64;
-    if (out.is_int) out.v.assign((size_t)n * n, 0);
-    else out.f.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < kNMax; ++i) out.rowmask[i] = out.colmask[i] = 0;
+    const size_t bytes = (size_t)n * n * 8;
+    unsigned char *buf;
+    if (storage) {
+        if (storage_bytes < bytes) { err = "ingest storage too small"; return PERM_ERR_SIZE; }
+        buf = static_cast<unsigned char *>(storage);
+    } else {
+        out.own.assign(bytes, 0);
+        buf = out.own.data();
+    }
+    std::memset(buf, 0, bytes);
+    out.f = out.is_int ? nullptr : reinterpret_cast<double *>(buf);
+    out.v = out.is_int ? reinterpret_cast<int64_t *>(buf) : nullptr;
     for (int o = 0; o < n; ++o) {
         const int b = A->ptr[o], e = A->ptr[o + 1];
         if (b > e || b < 0 || e > A->nnz) { err = "ptr not monotone"; return PERM_ERR_PATTERN; }
@@ -79,11 +91,20 @@ void order_none(const Matrix &m, int *col_order) {
     for (int j = 0; j < m.n; ++j) col_order[j] = j;
 }
 
+// Ascending nonzero count, ties by index (a stable insertion sort: n <= 64,
+// and it allocates nothing).
 void order_degree(const Matrix &m, int *col_order) {
     order_none(m, col_order);
-    std::stable_sort(col_order, col_order + m.n, [&](int a, int b) {
-        return __builtin_popcountll(m.colmask[a]) < __builtin_popcountll(m.colmask[b]);
-    });
+    for (int i = 1; i < m.n; ++i) {
+        const int c = col_order[i];
+        const int d = __builtin_popcountll(m.colmask[c]);
+        int j = i - 1;
+        while (j >= 0 && __builtin_popcountll(m.colmask[col_order[j]]) > d) {
+            col_order[j + 1] = col_order[j];
+            --j;
+        }
+        col_order[j + 1] = c;
+    }
 }
 
 // Algorithm 3 (PermanentOrdering).  cdeg[j] counts the nonzeros of column j

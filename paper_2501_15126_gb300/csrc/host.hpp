@@ -21,20 +21,30 @@ constexpr int kSMCount = 152;         // GB300
 constexpr int kRegsPerSM = 65536;
 constexpr int kMaxThreadsPerSM = 2048;
 
+// A dense copy of the input.  The n*n entries live either in the matrix's own
+// vector or in caller storage (the allocation-free entry point); the matrix is
+// not copyable because it may point into its own vector.
 struct Matrix {
     int n = 0;
     bool is_int = false;
-    std::vector<double> f;    // n*n row-major (FP64 inputs)
-    std::vector<int64_t> v;   // n*n row-major (integer inputs)
+    double *f = nullptr;      // n*n row-major (FP64 inputs)
+    int64_t *v = nullptr;     // n*n row-major (integer inputs)
+    std::vector<unsigned char> own;
     uint64_t rowmask[kNMax] = {};
     uint64_t colmask[kNMax] = {};
+    Matrix() = default;
+    Matrix(const Matrix &) = delete;
+    Matrix &operator=(const Matrix &) = delete;
     bool nz(int i, int j) const { return (rowmask[i] >> j) & 1ull; }
     double fval(int i, int j) const { return is_int ? (double)v[(size_t)i * n + j] : f[(size_t)i * n + j]; }
     int64_t ival(int i, int j) const { return v[(size_t)i * n + j]; }
 };
 
-// Copies and validates a borrowed matrix.  Explicit zeros are dropped.
-perm_status_t ingest(const perm_matrix_t *A, Matrix &out, std::string &err);
+// Copies and validates a borrowed matrix.  Explicit zeros are dropped.  With
+// `storage` (at least n*n*8 bytes) nothing is allocated.  *err is set to a
+// static message on failure.
+perm_status_t ingest(const perm_matrix_t *A, Matrix &out, const char **err, void *storage = nullptr,
+                     size_t storage_bytes = 0);
 
 // Dense row-major input (internal use by the batch path and tests).
 bool has_perfect_matching(const Matrix &m);

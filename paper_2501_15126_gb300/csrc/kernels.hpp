@@ -29,6 +29,10 @@ GenericFns generic_fns(int nmax, int arith);
 cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, uint64_t ntasks,
                                 const uint64_t *task_out, uint64_t *result, cudaStream_t st);
 
+// Serving: result[4 m ..] = sum of pool task results [seg[2m], seg[2m] + seg[2m+1]).
+cudaError_t segment_reduce_launch(int arith, const uint64_t *seg, int nseg, const uint64_t *pool, uint64_t *result,
+                                  cudaStream_t st);
+
 // Sums ntasks task results (words per task: 2 for FP64, arith for exact) in a
 // fixed order into result.
 cudaError_t reduce_launch(int arith, const uint64_t *task_out, uint64_t ntasks, uint64_t *result, cudaStream_t st);

@@ -46,12 +46,15 @@ namespace perm {
 constexpr size_t kWsBatchMat = 8;
 constexpr size_t kWsTaskOut = 16;
 
+perm_status_t fail(perm_status_t s, const char *msg);
 perm_status_t fail(perm_status_t s, const std::string &msg);
 perm_status_t cuda_fail(cudaError_t e, const char *what);
 double now_ms();
 
 // Stages of perm_plan_create / perm_compute, reused by batch and serving.
-perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_s &P);
+// storage: optional caller memory (>= n*n*8 bytes) for the dense copy.
+perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_s &P,
+                           void *storage = nullptr, size_t storage_bytes = 0);
 perm_status_t plan_device_setup(perm_plan_s &P);
 perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st);
 perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out);
@@ -59,5 +62,8 @@ void describe(const perm_plan_s &P, perm_result_t *out);
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);
 int nmax_bucket(int n);
 void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img);
+size_t devmat_bytes(int arith, int nmax);
+void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, unsigned char *dst);
+perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block);
 
 }  // namespace perm

@@ -1,0 +1,166 @@
+"""Host-side preprocessing checked against the paper: Theorem 1 / SCBS
+(Sec. IV), the 5-thread chunk table, Lemma 1 and Lemma 2 counts, Algorithm 2
+launch lists, Algorithm 3 ordering, Algorithm 4 partitioning, the structural
+guard and the exact-width choice.  CPU only (inspection calls)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2501_15126_gb300 import _abi as A
+from paper_2501_15126_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split(":", 1)
+        out[k.strip()] = [int(t) for t in v.replace(",", " ").split()]
+    return out
+
+
+def signed(seq):
+    return [s for s in seq]
+
+
+def test_scbs_matches_the_paper():
+    g = golden("scbs_sec4.txt")
+    for k in (2, 3, 4):
+        assert A.scbs(k) == g["scbs%d" % k]
+
+
+def test_changed_bit_sequence_n5():
+    g = golden("scbs_sec4.txt")
+    assert [abs(v) - 1 for v in A.scbs(4)] == g["changed_bits_n5"]
+
+
+def test_five_thread_chunk_table():
+    """5 threads, chunks of 3 iterations of SCBS(4) (Sec. IV): the signed kernel
+    calls per local iteration and the number of distinct ones."""
+    g = golden("scbs_sec4.txt")
+    seq = A.scbs(4)
+    table = [[seq[t * 3 + l] for t in range(5)] for l in range(3)]
+    assert table[0] == g["chunk3_row0"]
+    assert table[1] == g["chunk3_row1"]
+    assert table[2] == g["chunk3_row2"]
+    assert [len(set(r)) for r in table] == g["chunk3_distinct"]
+
+
+def test_theorem1_recursive_construction():
+    """SCBS(k) = [SCBS(k-1), +(k-1), -SCBS(k-1)^R] (Sec. IV) against Theorem 1."""
+    prev = A.scbs(1)
+    assert prev == [1]
+    for k in range(2, 15):
+        rec = prev + [k] + [-v for v in reversed(prev)]
+        assert A.scbs(k) == rec
+        prev = rec
+
+
+def test_lemma1_power_of_two_chunks():
+    """Chunks of 2^k: all threads of a warp share the column at every local step
+    except l = 2^(k-1) (same column, sign = parity of t) and l = 2^k."""
+    seq = A.scbs(16)
+    for k in (3, 5, 7):
+        c = 1 << k
+        for l in range(1, c + 1):
+            vals = [seq[l + t * c - 1] for t in range(32) if l + t * c - 1 < len(seq)]
+            cols = {abs(v) for v in vals}
+            if l == c // 2:
+                assert cols == {k} and {v > 0 for v in vals} == {True, False}
+                assert all((v > 0) == (t % 2 == 0) for t, v in enumerate(vals))
+            elif l == c:
+                assert len(cols) > 1
+            else:
+                assert len(set(vals)) == 1
+
+
+def test_lemma2_column_frequencies():
+    for n in (6, 11, 17):
+        seq = A.scbs(n - 1)
+        for j in range(n - 1):
+            assert sum(1 for v in seq if abs(v) - 1 == j) == 2 ** (n - j - 2)
+
+
+def test_algorithm2_launch_lists():
+    g = golden("alg2_launches.txt")
+    assert A.alg2_launches(2, 12) == [tuple(g["tau2_n12"])]
+    # every launch list covers [1, 2^(n-1)) with power-of-two chunks >= 1024 except possibly the last
+    for tau, n in ((69120, 40), (55296, 45), (124416, 48), (1000, 30)):
+        ls = A.alg2_launches(tau, n)
+        start = 1
+        for (s, d, e) in ls:
+            assert s == start and e == 1 << (n - 1)
+            assert d >= 1024 and d & (d - 1) == 0
+            start = s + tau * d
+        assert start >= 1 << (n - 1) or ls[-1][1] == 1024
+
+
+def test_algorithm3_ordering_picks_min_unordered_degree():
+    # a small matrix traced by hand: column degrees 3,1,2,3 ...
+    a = np.array([[1, 0, 1, 0],
+                  [1, 0, 0, 1],
+                  [1, 1, 0, 1],
+                  [0, 0, 1, 1]], dtype=np.int64)
+    ins = A.inspect(a, ordering=A.PERM_ORDER_PAPER)
+    # round 1: min cdeg is column 1 (1 nonzero) -> row 2 ordered; cdeg[0]=2, cdeg[3]=2, cdeg[2]=2
+    # round 2: ties at 2 -> smallest index, column 0 -> rows 0, 1; cdeg[2]=1, cdeg[3]=1
+    # round 3: column 2 (1) -> row 3; round 4: column 3
+    assert list(ins.col_order)[:4] == [1, 0, 2, 3]
+    assert list(ins.row_order)[:4] == [2, 0, 1, 3]
+    assert list(ins.group_size)[:4] == [1, 2, 1, 0]
+
+
+def test_orderings_and_cost_model():
+    a = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
+    deg = A.inspect(a, ordering=A.PERM_ORDER_DEGREE)
+    pap = A.inspect(a, ordering=A.PERM_ORDER_PAPER)
+    auto = A.inspect(a)
+    nnz = [int((a[:, j] != 0).sum()) for j in range(36)]
+    assert [nnz[c] for c in list(deg.col_order)[:36]] == sorted(nnz)
+    assert auto.ops_per_step == min(deg.ops_per_step, pap.ops_per_step)
+    assert pap.ops_per_step < pap.ops_per_step_paper
+    assert sum(list(pap.group_size)[:36]) == 36
+    # every row's group is the first ordered column that touches it
+    order = list(pap.col_order)[:36]
+    for slot in range(36):
+        r = pap.row_order[slot]
+        first = min(p for p in range(36) if a[r, order[p]] != 0)
+        assert pap.group_of_row[slot] == first
+
+
+def test_algorithm4_partition_is_consistent():
+    a = synth.band_plus(48, 3, 2, seed=3, values="01")
+    ins = A.inspect(a, ordering=A.PERM_ORDER_PAPER)
+    k, c = ins.reg_rows, ins.reg_cols
+    assert 1 <= c <= 47 and 1 <= k <= 48
+    assert k == sum(list(ins.group_size)[:c])   # k = rows touched by the first c columns
+
+
+def test_structural_guard_and_exact_width():
+    z = np.eye(5, dtype=np.int64)
+    z[:, 0] = 1
+    z[0, :] = 1
+    z[1, 1] = 0
+    z[2, 2] = 0      # rows 1, 2 only reach column 0 -> no perfect matching
+    assert A.inspect(z).structurally_zero == 1
+    assert A.inspect(np.eye(5, dtype=np.int64)).structurally_zero == 0
+    a = synth.single_er(24, 0.2, 1, values="01")
+    assert A.inspect(a).exact_words == 1
+    b = synth.band_plus(48, 3, 2, seed=3, values="01")
+    assert A.inspect(b).exact_words == 3
+    ones = synth.ones(30)
+    # Bregman: perm(J_30) = 30! ~ 2^107.7; the bound must cover it
+    assert A.inspect(ones).bound_log2 >= np.log2(float(np.prod(np.arange(1, 31, dtype=float)))) - 1e-9
+
+
+def test_codegen_source_bakes_the_matrix():
+    a = synth.single_er(12, 0.3, 5, values="f64")
+    src = A.codegen_source(a)
+    assert "perm_walk" in src and "x[0]" in src and "0x1." in src
+    srck = A.codegen_source(a, reg_rows=6)
+    assert "xg[" in srck
