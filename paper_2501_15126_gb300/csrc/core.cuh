@@ -304,7 +304,10 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
             QB = pol.chain_hi(j, x);
         }
         const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
-        if (zero_skip && __all_sync(PERM_FULLMASK, A::is_zero(QB))) {
+        // The vote runs every block, skip or not: it is also the point where
+        // the warp reconverges after the data-driven loops of a flip.
+        const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(QB));
+        if (zero_skip && all_zero) {
             // every product of this block is zero; apply the block's net flip
             pol.template flip_rt<Bv - 1>(x, s_mid);
             ++skipped;

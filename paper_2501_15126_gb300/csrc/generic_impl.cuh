@@ -26,9 +26,9 @@ namespace pk {
 // with a compile-time k, so x stays in registers.  The switch argument is
 // warp-uniform (a bit of a column or group mask), so it is a uniform jump,
 // and only the slots a column really touches cost an arithmetic instruction.
-// Each data-driven loop ends in __syncwarp(): the compiler cannot prove the
-// masks uniform, and without an explicit reconvergence point the warp's
-// lanes can drift apart and run the loops one path at a time.
+// The compiler cannot prove the masks uniform; the walk's once-per-block
+// warp vote (core.cuh) is the reconvergence point that keeps the lanes
+// together.
 // (A predicated loop over all NMAX slots would issue NMAX FP64 instructions
 // per flip whatever the mask: on GB300, where FP64 issues at 1/64 of FP32,
 // that dominates everything else.)
@@ -97,7 +97,6 @@ struct GenericPol {
             cm &= cm - 1;
             add_slot_s<S>(x, i, v[i]);
         }
-        __syncwarp();
     }
     template <int J>
     __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
@@ -109,7 +108,6 @@ struct GenericPol {
             cm &= cm - 1;
             add_slot(x, i, v[i], s);
         }
-        __syncwarp();
     }
     __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
         u64 gm = ((const volatile u64 *)m->grpmask)[g];
@@ -118,7 +116,6 @@ struct GenericPol {
             gm &= gm - 1;
             q = A::mul(q, get_slot(x, i));
         }
-        __syncwarp();
         return q;
     }
     template <int G>

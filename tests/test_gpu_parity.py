@@ -197,3 +197,35 @@ def test_cfg3_subranges_exact_and_f64():
         subrange_check_exact(a01, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN, reg_rows=20)
         subrange_check_f64(af, lo, lo + span, engine=A.PERM_ENGINE_CODEGEN, reg_rows=20)
     subrange_check_exact(a01, 1 << 30, (1 << 30) + span, engine=A.PERM_ENGINE_GENERIC)
+
+
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
+def test_band_only_sibling_full_walk_against_band_dp(engine):
+    """Band-only matrices (|i-j| <= 3, no off-band entries) walked in full on the
+    GPU and checked against the banded DP, an algorithm independent of Ryser:
+    n=32 (2^31 Gray steps) exact and FP64, and n=36 exact through codegen."""
+    a01 = synth.band_plus(32, 3, 0, seed=3, values="01")
+    af = synth.band_plus(32, 3, 0, seed=3, values="f64")
+    assert A.permanent(a01, engine=engine).value == oracle.band_dp_int(a01, 3)
+    want = float(oracle.band_dp(af, 3))
+    assert rel_err(A.permanent(af, engine=engine).value, want) <= RTOL
+    if engine == A.PERM_ENGINE_CODEGEN:
+        b01 = synth.band_plus(36, 3, 0, seed=13, values="01")
+        assert A.permanent(b01, engine=engine).value == oracle.band_dp_int(b01, 3)
+
+
+def test_cfg2_full_permanent_against_stored_oracle_value():
+    """The n=36 workload at full size, in the launch configuration bench.py
+    times, against the oracle's full-range value stored in tests/golden."""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "cfg2_n36.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        vals[k] = float(v)
+    want = vals["perm_hi"] + vals["perm_lo"]
+    a = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
+    r = A.permanent(a)
+    assert r.engine == A.PERM_ENGINE_CODEGEN
+    assert rel_err(r.value, want) <= RTOL, (r.value, want)
