@@ -176,6 +176,22 @@ void perm_plan_destroy(perm_plan_t plan);
 perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
                          void *stream, perm_result_t *out);
 
+/* One permanent without allocating anything, for callers that may not
+   allocate device memory (a framework that owns the memory pool, a process
+   that reserved all HBM up front, code that must not call cudaMalloc or
+   cudaFree).  The paper has no counterpart: it is a packaging of the
+   precompiled walk.  Its scratch memory is a file-scope device array of
+   1 MiB that every GPU loading the library holds until exit; host
+   temporaries live on the stack.  n <= 48 (PERM_ERR_SIZE beyond), generic
+   kernels only (engine CODEGEN gives PERM_ERR_ARG).  The first call on a
+   device looks up the array's device address with that device current, so
+   make it before any stream capture.  All calls share the array: two calls
+   whose GPU work overlaps race.  Results match perm_plan_create +
+   perm_compute; ms_kernel is not measured (0).  The call synchronises
+   `stream`. */
+perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm_opts_t *opts, void *stream,
+                                   perm_result_t *out);
+
 /* Same as perm_batch, but each matrix gets its own plan and its own launches
    (the plain one-launch-per-matrix form, for comparison). */
 perm_status_t perm_batch_sequential(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,

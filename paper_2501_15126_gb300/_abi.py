@@ -105,6 +105,7 @@ SIGNATURES = [
     ("perm_version", ctypes.c_char_p, []),
     ("perm_sizeof", c_i64, [c_i32]),
     ("perm_issue_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
+    ("perm_compute_noalloc", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), c_vp, ctypes.POINTER(Result)]),
 ]
 
 _lib = None
@@ -200,6 +201,16 @@ def permanent(a, stream: int = 0, **kw) -> Result:
         return p.compute(stream)
     finally:
         p.close()
+
+
+def permanent_noalloc(a, stream: int = 0, **kw) -> Result:
+    """perm_compute_noalloc: the same permanent without any allocation."""
+    m = a if isinstance(a, CSRMatrix) else CSRMatrix(a)
+    o = opts(**kw)
+    r = Result()
+    check(lib().perm_compute_noalloc(ctypes.byref(m.c), ctypes.byref(o), c_vp(stream), ctypes.byref(r)),
+          "perm_compute_noalloc")
+    return r
 
 
 def inspect(a, **kw) -> Inspect:

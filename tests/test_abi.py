@@ -22,7 +22,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("perm_plan_create", "perm_compute", "perm_plan_destroy", "perm_batch", "perm_submit", "perm_poll",
-                 "perm_server_create", "perm_server_destroy"):
+                 "perm_server_create", "perm_server_destroy", "perm_compute_noalloc"):
         assert must in names
 
 
@@ -59,3 +59,5 @@ def test_bad_arguments_fail_without_a_gpu():
     assert L.perm_plan_create(ctypes.byref(rep.c), None, ctypes.byref(h)) == A.PERM_ERR_PATTERN
     big = A.CSRMatrix(n=65, ptr=list(range(66)), idx=list(range(65)), vals=[1.0] * 65, vtype=A.PERM_F64)
     assert L.perm_plan_create(ctypes.byref(big.c), None, ctypes.byref(h)) == A.PERM_ERR_SIZE
+    r = A.Result()
+    assert L.perm_compute_noalloc(ctypes.byref(big.c), None, None, ctypes.byref(r)) == A.PERM_ERR_SIZE
