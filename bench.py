@@ -406,7 +406,7 @@ def run_profile_case(args):
     if args.profile_exact:
         from paper_2501_15126_gb300 import synth
         a = synth.band_plus(48, 3, 2, seed=3, values="01")
-    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2)
+    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2, engine=A.PERM_ENGINE_CODEGEN)
     for _ in range(args.steps):
         r = p.compute()
     print(json.dumps({"profile_case": vals, "gray_steps": r.steps, "ms_kernel": r.ms_kernel,

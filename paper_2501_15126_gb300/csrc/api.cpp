@@ -269,6 +269,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
         normalise_split(P.L, &k, &c);
         P.k = k;
         P.c = c;
+        if (P.arith == 0) P.ops_per_step = cost_per_step_paired(P.L);
         std::string err;
         perm_status_t st = codegen_build(P, err);
         if (st != PERM_OK) return fail(st, err);

@@ -155,6 +155,8 @@ struct Emitter {
         else o << "typedef ArithExact<" << P.arith << "> A;\n";
         o << "struct GenPol {\n";
         o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
+        o << "    static constexpr bool kPaired = " << (P.arith == 0 ? "true" : "false") << ";\n";
+        o << "    static constexpr bool kRolled = false;\n";
         o << "    typedef A::X X;\n    typedef A::P P;\n";
         o << "    X *xg;\n    unsigned long long stride;\n";
         for (int g : hi) o << "    P Q" << g << ";\n";
@@ -185,6 +187,33 @@ struct Emitter {
             o << "            break;\n";
         }
         o << "        default: break;\n        }\n    }\n";
+        // paired steps (FP64): D = prod_{R_0} x - prod_{R_0} (x + S a_0), the
+        // column-0 flip applied, Q_1 * D returned.  R_0 = column 0's rows = the
+        // first slots.
+        if (P.arith == 0) {
+            const int r0 = P.L.group_begin[1] - P.L.group_begin[0];
+            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1) {\n";
+            if (r0 == 1) {
+                const std::string v = lit(P, value(0, 0));
+                o << "        if constexpr (S > 0) { x[0] += " << v << "; return q1 * -" << v << "; }\n";
+                o << "        else { x[0] -= " << v << "; return q1 * " << v << "; }\n";
+            } else {
+                o << "        P px = x[0];\n";
+                for (int s2 = 1; s2 < r0 - 1; ++s2) o << "        px = px * x[" << s2 << "];\n";
+                o << "        const X xl = x[" << r0 - 1 << "];\n";
+                o << "        if constexpr (S > 0) {\n";
+                for (int s2 = 0; s2 < r0; ++s2) o << "            x[" << s2 << "] += " << lit(P, value(0, s2)) << ";\n";
+                o << "        } else {\n";
+                for (int s2 = 0; s2 < r0; ++s2) o << "            x[" << s2 << "] -= " << lit(P, value(0, s2)) << ";\n";
+                o << "        }\n";
+                o << "        P py = x[0];\n";
+                for (int s2 = 1; s2 < r0; ++s2) o << "        py = py * x[" << s2 << "];\n";
+                o << "        return q1 * fma(px, xl, -py);\n";
+            }
+            o << "    }\n";
+        } else {
+            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1) { return q1; }\n";
+        }
         // group products of the low levels
         o << "    template <int M> __device__ __forceinline__ P grp(const X (&x)[NX], P q) const {\n";
         for (int g = 0; g < B; ++g) {
@@ -226,20 +255,25 @@ struct Emitter {
             o << "        Q" << g << " = q;\n";
         }
         o << "        return q;\n    }\n";
+        // After a flip of column j >= B: rebuild levels j, j-1, ..., B.  The
+        // first switch loads the stored level just above j; the second falls
+        // through from case j down to case B, so every level's code appears
+        // once (the source and the compile time stay linear in n).
         o << "    __device__ __forceinline__ P chain_hi(int j, const X (&x)[NX]) {\n";
         o << "        P q;\n        switch (j) {\n";
-        for (int j = B; j < n - 1; ++j) {
+        for (int j = B; j < n - 1; ++j) o << "        case " << j << ": q = " << above(j) << "; break;\n";
+        o << "        default: q = A::one(); break;\n        }\n";
+        o << "        switch (j) {\n";
+        for (int j = n - 2; j >= B; --j) {
             o << "        case " << j << ":\n";
-            o << "            q = " << above(j) << ";\n";
-            for (int g : hi) {
-                if (g > j) continue;
-                group_product(g, "            ");
-                o << "            Q" << g << " = q;\n";
+            if (P.L.group_begin[j + 1] > P.L.group_begin[j]) {
+                group_product(j, "            ");
+                o << "            Q" << j << " = q;\n";
             }
-            o << "            return q;\n";
+            o << "            [[fallthrough]];\n";
         }
-        o << "        default: return " << (hi.empty() ? std::string("A::one()") : "Q" + std::to_string(hi.back()))
-          << ";\n        }\n    }\n";
+        o << "        default: break;\n        }\n";
+        o << "        return q;\n    }\n";
         o << "};\n}  // namespace pk\n\n";
         o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock
           << ") perm_walk(pk::WalkArgs wa, void *xg_base) {\n";

@@ -282,6 +282,55 @@ struct BlockSteps {
     }
 };
 
+// Paired form (policies with kPaired): an even step l (flip of column
+// J = ctz(l) >= 1, then levels J..1 rebuilt) and the odd step l+1 (flip of
+// column 0, sign bit 1 of l+1) differ only in the rows of R_0, which are
+// exactly column 0's rows, so their two terms combine into
+//   (-1)^l (P(l) - P(l+1)) = Q_1 (prod_{R_0} x - prod_{R_0} (x + s a_0)),
+// formed once by the policy's pair<s>() (which also applies the column-0
+// flip).  Same terms, about 1.5 fewer multiply/add operations per step.
+template <class Pol, class A, int Bv, int Lstep>
+struct PairSteps {
+    static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
+                                               typename A::Blk &blk, int s_mid) {
+        if constexpr (Lstep < (1 << Bv)) {
+            constexpr int J = Ctz<Lstep>::v;     // >= 1: Lstep is even
+            if constexpr (J == Bv - 1) {
+                pol.template flip_rt<J>(x, s_mid);
+            } else {
+                constexpr int S = ((Lstep >> (J + 1)) & 1) ? -1 : 1;
+                pol.template flip<J, S>(x);
+            }
+            LevelsDown<Pol, A, Bv, J>::run(pol, x, Q);
+            constexpr int S0 = (((Lstep + 1) >> 1) & 1) ? -1 : 1;
+            A::template blk_add<1>(blk, pol.template pair<S0>(x, Q[1]));
+            PairSteps<Pol, A, Bv, Lstep + 2>::run(pol, x, Q, blk, s_mid);
+        }
+    }
+};
+
+// Rolled form (policies with kRolled): the same 2^B steps as BlockSteps,
+// but as a loop with the column chosen at run time.  A data-driven policy
+// (the precompiled generic kernels) gains nothing from unrolling and loses
+// instruction-cache hits to it, so it takes this form; levels 1..B-1 of the
+// chain stay in registers (every Q index is a compile-time constant).
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ void rolled_block(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
+                                             typename A::Blk &blk, int s_mid) {
+#pragma unroll 1
+    for (int l = 1; l < (1 << Bv); ++l) {
+        const int j = __ffs(l) - 1;
+        const int s = (j == Bv - 1) ? s_mid : (((l >> (j + 1)) & 1) ? -1 : 1);
+        pol.flip_dyn(j, x, s);
+#pragma unroll
+        for (int M = Bv - 1; M >= 1; --M)
+            if (M <= j) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
+        const typename A::P p = pol.grp_dyn(0, x, Q[1]);
+        if (l & 1) A::template blk_add<-1>(blk, p);
+        else A::template blk_add<1>(blk, p);
+    }
+}
+
 // ------------------------------------------------------------------ one chunk
 // Walks Gray indices [q 2^K, (q+1) 2^K) and returns sum (-1)^g prod_i x_i(g).
 
@@ -315,10 +364,21 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
         }
         P Q[Bv + 1];
         Q[Bv] = QB;
-        LevelsDown<Pol, A, Bv, Bv - 1>::run(pol, x, Q);
+        if constexpr (!Pol::kRolled) LevelsDown<Pol, A, Bv, Bv - 1>::run(pol, x, Q);
         typename A::Blk blk = A::blk_zero();
-        A::template blk_add<1>(blk, pol.template grp<0>(x, Q[1]));
-        BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
+        if constexpr (Pol::kRolled) {
+#pragma unroll
+            for (int M = Bv - 1; M >= 1; --M) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
+            A::template blk_add<1>(blk, pol.grp_dyn(0, x, Q[1]));
+            rolled_block<Pol, A, Bv>(pol, x, Q, blk, s_mid);
+        } else if constexpr (Pol::kPaired) {
+            // steps 0 and 1 (column 0, sign +: bit 1 of 1 is 0), then pairs (2,3), (4,5), ...
+            A::template blk_add<1>(blk, pol.template pair<1>(x, Q[1]));
+            PairSteps<Pol, A, Bv, 2>::run(pol, x, Q, blk, s_mid);
+        } else {
+            A::template blk_add<1>(blk, pol.template grp<0>(x, Q[1]));
+            BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
+        }
         A::acc_merge(acc, blk);
     }
     return acc;

@@ -1,5 +1,5 @@
 // generic_f64.cu -- generic kernels for one arithmetic (see generic_impl.cuh).
-#define PERM_GENERIC_B 4
+#define PERM_GENERIC_B 5
 #include "generic_impl.cuh"
 
 PERM_GENERIC_UNIT(f64, pk::ArithF64)

@@ -41,6 +41,8 @@ template <int NMAX, class A>
 struct GenericPol {
     static constexpr int NX = NMAX;
     static constexpr int Bv = PERM_GENERIC_B;
+    static constexpr bool kPaired = false;
+    static constexpr bool kRolled = true;
     typedef typename A::X X;
     typedef typename A::P P;
     typedef typename A::V V;

@@ -207,6 +207,22 @@ double cost_per_step(const Layout &L, bool paper_scheme) {
     return total;
 }
 
+double cost_per_step_paired(const Layout &L) {
+    const int n = L.n;
+    if (n < 3) return cost_per_step(L, false);
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    const double r0 = L.group_begin[1] - L.group_begin[0];
+    double total = 0.0, prefix = 0.0;
+    for (int j = 1; j <= n - 2; ++j) {
+        const double w = std::ldexp(1.0, n - j - 2) / steps;   // Lemma 2
+        prefix += L.group_begin[j + 1] - L.group_begin[j];     // |R_1| + ... + |R_j|
+        total += w * (L.col_nnz[j] + prefix);
+    }
+    const double w0 = std::ldexp(1.0, n - 2) / steps;           // column-0 steps = pairs
+    const double pair_ops = r0 == 1 ? 2.0 : 3.0 * r0 - 1.0;
+    return total + w0 * pair_ops;
+}
+
 Layout choose_layout(const Matrix &m, int ordering_opt) {
     int cols[kNMax], rows[kNMax];
     if (ordering_opt == PERM_ORDER_NONE) { order_none(m, cols); return make_layout(m, cols, PERM_ORDER_NONE); }

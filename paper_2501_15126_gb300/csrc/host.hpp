@@ -76,6 +76,11 @@ Layout make_layout(const Matrix &m, const int *col_order, int ordering);
 // chain scheme: nnz_j updates + |R_0|+...+|R_j| multiplies + 1 accumulate;
 // paper scheme: nnz_j updates + (n-1) multiplies + 1 accumulate.
 double cost_per_step(const Layout &L, bool paper_scheme);
+// The same walk with even/odd steps paired (the generated FP64 kernels):
+// per pair, column 0's r = |R_0| updates, 2r-2 multiplies/fused multiply-adds
+// for prod x - prod (x + s a_0), and one fused multiply-add into the sum; the
+// even step's flip rebuilds levels j..1 only.
+double cost_per_step_paired(const Layout &L);
 
 // Chooses the ordering (AUTO = cheaper of DEGREE and PAPER under the model).
 Layout choose_layout(const Matrix &m, int ordering_opt);
