@@ -294,6 +294,15 @@ def run_batch(args):
         t0 = time.perf_counter()
         res = A.batch(mats, stream=stream.cuda_stream)
         times.append(time.perf_counter() - t0)
+    # the two arithmetic halves on their own (each is its own kernel family)
+    split = {}
+    for vals in ("f64", "01"):
+        sub = [m for m, it in zip(mats, items) if it.values == vals]
+        sub_steps = sum(1 << (it.n - 1) for it in items if it.values == vals)
+        t0 = time.perf_counter()
+        A.batch(sub, stream=stream.cuda_stream)
+        dt = time.perf_counter() - t0
+        split[vals] = {"count": len(sub), "seconds": dt, "gray_steps_per_s": sub_steps / dt}
     seq_t0 = time.perf_counter()
     seq = A.batch(mats, sequential=True, stream=stream.cuda_stream)
     seq_time = time.perf_counter() - seq_t0
@@ -310,7 +319,7 @@ def run_batch(args):
             "config": {"workload": "batch of %d ER matrices, n uniform in [12,28], p uniform in [0.2,0.4] + forced "
                                    "diagonal, alternating 0/1 (exact) and (0,1] (FP64), seed 4" % len(items),
                        "gray_steps_total": steps_total, "l2": "inputs re-uploaded every step"},
-            "gray_steps_per_s": steps_total / best,
+            "gray_steps_per_s": steps_total / best, "by_arithmetic": split,
             "sequential": {"seconds": seq_time, "perms_per_s": len(items) / seq_time,
                            "note": "perm_batch_sequential: plan + launch + sync + destroy per matrix"},
             "speedup_vs_sequential": seq_time / best,
@@ -374,8 +383,27 @@ def run_serving(args):
             lat[i] = time.perf_counter() - (t0 + arrivals[i])
         return lat, res, time.perf_counter() - t0
 
+    def capacity_server():
+        """Closed loop: every request submitted at once; time until all are done."""
+        with A.Server() as s:
+            for m in mats[:50]:
+                s.poll(s.submit(m), 60000)
+            t0 = time.perf_counter()
+            tickets = [s.submit(m) for m in mats]
+            for t in tickets:
+                s.poll(t, -1)
+            return len(mats) / (time.perf_counter() - t0)
+
+    def capacity_sequential():
+        t0 = time.perf_counter()
+        for m in mats:
+            A.permanent(m)
+        return len(mats) / (time.perf_counter() - t0)
+
     ls, rs, ws = replay_server()
     lq, rq, wq = replay_sequential()
+    cap_s = capacity_server()
+    cap_q = capacity_sequential()
     q = lambda v, p: float(np.percentile(np.array(v) * 1e3, p))
     bad = [(i, reqs[i].a.shape[0], reqs[i].values, a.status, a.value, b.value) for i, (a, b) in enumerate(zip(rs, rq))
            if a.status or b.status or (a.value != b.value if a.vtype == 1 else abs(a.value - b.value) > 1e-9 * abs(b.value))]
@@ -390,6 +418,8 @@ def run_serving(args):
             "p50_ms": q(ls, 50), "p99_ms": q(ls, 99), "max_ms": q(ls, 100),
             "sequential": {"perms_per_s": len(reqs) / wq, "p50_ms": q(lq, 50), "p99_ms": q(lq, 99),
                            "max_ms": q(lq, 100)},
+            "capacity_perms_per_s": {"server": cap_s, "sequential": cap_q, "ratio": cap_s / cap_q,
+                                     "note": "closed loop: the same requests submitted all at once"},
             "mismatches_vs_sequential": mism, "mismatch_examples": [list(map(str, b)) for b in bad[:5]]}
     print(json.dumps(line))
     return 0
@@ -406,10 +436,11 @@ def run_profile_case(args):
     if args.profile_exact:
         from paper_2501_15126_gb300 import synth
         a = synth.band_plus(48, 3, 2, seed=3, values="01")
-    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2, engine=A.PERM_ENGINE_CODEGEN)
+    engine = A.PERM_ENGINE_GENERIC if args.profile_engine == "generic" else A.PERM_ENGINE_CODEGEN
+    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2, engine=engine)
     for _ in range(args.steps):
         r = p.compute()
-    print(json.dumps({"profile_case": vals, "gray_steps": r.steps, "ms_kernel": r.ms_kernel,
+    print(json.dumps({"profile_case": vals, "engine": args.profile_engine, "gray_steps": r.steps, "ms_kernel": r.ms_kernel,
                       "ops_per_step": r.fp_ops_per_step, "threads": r.threads, "regs": r.regs_per_thread,
                       "chunk_log2": r.chunk_log2, "zero_skip_frac": r.zero_skip_frac}))
     p.close()
@@ -427,6 +458,7 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile"])
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
+    ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)

@@ -54,13 +54,26 @@ int nmax_bucket(int n) {
 static int floor_log2(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
 
 // Builds the shared-memory image read by the generic kernels.
-size_t devmat_bytes(int arith, int nmax) {
+// Image layout (see devmat.h): 16-byte header, column masks, group masks,
+// column offsets (u16), x0, then the values of columns 0..n-2 in slot order.
+static size_t devmat_head(int nmax) { return 16 + 16 * (size_t)nmax + 2 * (size_t)nmax; }
+
+size_t devmat_bytes(int arith, int nmax, int nnz) {
     const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
-    return 16 + 8 * (size_t)nmax * 2 + vsz * (size_t)nmax * (1 + (size_t)nmax);
+    const size_t b = devmat_head(nmax) + vsz * (size_t)nmax + vsz * (size_t)nnz;
+    return (b + 15) & ~(size_t)15;
 }
 
+static int devmat_nnz(const Layout &L) {
+    int nnz = 0;
+    for (int p = 0; p + 1 < L.n; ++p) nnz += L.col_nnz[p];
+    return nnz;
+}
+
+size_t devmat_bytes_for(const Layout &L, int arith, int nmax) { return devmat_bytes(arith, nmax, devmat_nnz(L)); }
+
 void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img) {
-    img.assign(devmat_bytes(arith, nmax), 0);
+    img.assign(devmat_bytes(arith, nmax, devmat_nnz(L)), 0);
     build_devmat_into(m, L, arith, nmax, img.data());
 }
 
@@ -68,18 +81,21 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
     const int n = m.n;
     const int last = L.col_order[n - 1];
     const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
-    const size_t head = 16 + 8 * (size_t)nmax * 2;
-    std::memset(dst, 0, devmat_bytes(arith, nmax));
-    unsigned char *base = dst;
-    int32_t *hdr = reinterpret_cast<int32_t *>(base);
+    const int nnz = devmat_nnz(L);
+    const size_t bytes = devmat_bytes(arith, nmax, nnz);
+    std::memset(dst, 0, bytes);
+    int32_t *hdr = reinterpret_cast<int32_t *>(dst);
     hdr[0] = n;
     hdr[1] = L.top;
-    uint64_t *colmask = reinterpret_cast<uint64_t *>(base + 16);
+    hdr[2] = nnz;
+    hdr[3] = (int32_t)bytes;
+    uint64_t *colmask = reinterpret_cast<uint64_t *>(dst + 16);
     uint64_t *grpmask = colmask + nmax;
+    uint16_t *colptr = reinterpret_cast<uint16_t *>(grpmask + nmax);
     for (int p = 0; p + 1 < n; ++p) colmask[p] = L.colmask[p];
     for (int g = 0; g < n; ++g)
         for (int s = L.group_begin[g]; s < L.group_begin[g + 1]; ++s) grpmask[g] |= 1ull << s;
-    unsigned char *x0 = base + head;
+    unsigned char *x0 = dst + devmat_head(nmax);
     unsigned char *val = x0 + vsz * nmax;
     for (int s = 0; s < n; ++s) {
         const int r = L.row_order[s];
@@ -95,14 +111,16 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
             std::memcpy(x0 + vsz * s, &v, vsz);
         }
     }
+    int k = 0;
     for (int p = 0; p + 1 < n; ++p) {
         const int c = L.col_order[p];
+        colptr[p] = (uint16_t)k;
         for (int s = 0; s < n; ++s) {
+            if (!((L.colmask[p] >> s) & 1ull)) continue;
             const int r = L.row_order[s];
-            if (!m.nz(r, c)) continue;
-            unsigned char *dst = val + vsz * ((size_t)p * nmax + s);
-            if (arith == 0) { const double v = m.fval(r, c); std::memcpy(dst, &v, vsz); }
-            else { const int v = (int)(2 * m.ival(r, c)); std::memcpy(dst, &v, vsz); }
+            unsigned char *d = val + vsz * (size_t)k++;
+            if (arith == 0) { const double v = m.fval(r, c); std::memcpy(d, &v, vsz); }
+            else { const int v = (int)(2 * m.ival(r, c)); std::memcpy(d, &v, vsz); }
         }
     }
 }
@@ -243,6 +261,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
         P.nmax = nmax;
         std::vector<unsigned char> img;
         build_devmat(P.m, P.L, P.arith, nmax, img);
+        P.img_bytes = img.size();
         if ((e = cudaMalloc(&P.d_devmat, img.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(devmat)");
         if ((e = cudaMemcpy(P.d_devmat, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpy(devmat)");
@@ -257,7 +276,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
             P.K = 0;
         } else {
             int bps = 0;
-            if ((e = P.gf.occ(256, &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
+            if ((e = P.gf.occ(256, img.size(), &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
             perm_status_t st = choose_launch(P, P.gf.block_log2, std::max(bps, 1), 256);
             if (st != PERM_OK) return st;
         }
@@ -318,7 +337,7 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st) {
         ba.task_counter = reinterpret_cast<unsigned long long *>(P.d_ws);
         ba.task_out = reinterpret_cast<unsigned long long *>(task_out);
         ba.skip_counter = reinterpret_cast<unsigned long long *>(P.d_ws + 1);
-        ba.devmat_stride = P.gf.devmat_bytes;
+        ba.slot_bytes = P.img_bytes;
         ba.nmat = 1;
         ba.zero_skip = P.opts.zero_skip ? 0 : 1;
         e = P.gf.walk(ba, P.grid, P.block, st);

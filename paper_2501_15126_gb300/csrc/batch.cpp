@@ -60,20 +60,25 @@ int BatchGroup::setup(int nmax_, int arith_, int K_target) {
         mats[i].chunk_lo = 0;
         mats[i].chunk_hi = P.chunk_hi;
         mats[i].out_offset = ntasks;
-        mats[i].image = (int)i;
         mats[i].K = K;
         ntasks += P.ntasks;
     }
-    images.assign(plans.size() * gf.devmat_bytes, 0);
-    std::vector<unsigned char> img;
+    // images packed back to back (each a multiple of 16 bytes)
+    size_t total = 0;
+    slot_bytes = 16;
     for (size_t i = 0; i < plans.size(); ++i) {
-        build_devmat(plans[i]->m, plans[i]->L, arith, nmax, img);
-        std::memcpy(images.data() + i * gf.devmat_bytes, img.data(), gf.devmat_bytes);
+        const size_t b = devmat_bytes_for(plans[i]->L, arith, nmax);
+        mats[i].image = (int)(total / 16);
+        total += b;
+        slot_bytes = std::max(slot_bytes, b);
     }
+    images.assign(total, 0);
+    for (size_t i = 0; i < plans.size(); ++i)
+        build_devmat_into(plans[i]->m, plans[i]->L, arith, nmax, images.data() + (size_t)mats[i].image * 16);
     cudaFuncAttributes attr;
     if (gf.attr(&attr) == cudaSuccess) regs = attr.numRegs;
     int bps = 0;
-    cudaError_t e = gf.occ(256, &bps);
+    cudaError_t e = gf.occ(256, slot_bytes, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     block = 256;
     int64_t g = (int64_t)kSMCount * std::max(bps, 1);
@@ -116,7 +121,7 @@ int BatchGroup::launch(cudaStream_t st, int zero_skip) {
     ba.task_counter = reinterpret_cast<unsigned long long *>(d_counters);
     ba.task_out = reinterpret_cast<unsigned long long *>(d_task_out);
     ba.skip_counter = reinterpret_cast<unsigned long long *>(d_counters + 1);
-    ba.devmat_stride = gf.devmat_bytes;
+    ba.slot_bytes = slot_bytes;
     ba.nmat = (int)mats.size();
     ba.zero_skip = zero_skip;
     if ((e = gf.walk(ba, grid, block, st)) != cudaSuccess) return cuda_fail(e, "batch walk launch");

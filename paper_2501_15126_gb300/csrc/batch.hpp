@@ -29,6 +29,7 @@ struct BatchGroup {
     std::vector<pk::BatchMat> mats;
     std::vector<unsigned char> images;
     uint64_t ntasks = 0;
+    size_t slot_bytes = 16;                // the largest image of the group
     int grid = 1, block = 256, regs = 0;
     unsigned char *d_images = nullptr;
     pk::BatchMat *d_mats = nullptr;

@@ -17,6 +17,7 @@
 // process.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <sstream>
@@ -85,6 +86,17 @@ std::string cu_err(CUresult r) {
 }
 
 // ------------------------------------------------------------------ source emission
+// Resident 256-thread blocks per SM that the generated kernel is compiled for
+// (its register budget: 2 -> 128 registers, 3 -> 85).  PERM_CODEGEN_MIN_BLOCKS
+// overrides the default of 2.
+int codegen_min_blocks(const perm_plan_s &) {
+    const char *e = std::getenv("PERM_CODEGEN_MIN_BLOCKS");
+    if (e) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 8) return v;
+    }
+    return 2;
+}
 std::string lit(const perm_plan_s &P, double v) {
     char buf[64];
     if (P.arith == 0) {
@@ -100,8 +112,9 @@ std::string lit(const perm_plan_s &P, double v) {
 struct Emitter {
     const perm_plan_s &P;
     int n, k, c;
+    int min_blocks;   // __launch_bounds__ minimum resident blocks per SM (register budget)
     std::ostringstream o;
-    explicit Emitter(const perm_plan_s &p) : P(p), n(p.m.n), k(p.k), c(p.c) {}
+    explicit Emitter(const perm_plan_s &p) : P(p), n(p.m.n), k(p.k), c(p.c), min_blocks(codegen_min_blocks(p)) {}
 
     // value of ordered column p at slot s (doubled on the exact path)
     bool has(int p, int s) const { return (P.L.colmask[p] >> s) & 1ull; }
@@ -275,7 +288,7 @@ struct Emitter {
         o << "        default: break;\n        }\n";
         o << "        return q;\n    }\n";
         o << "};\n}  // namespace pk\n\n";
-        o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock
+        o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock << ", " << min_blocks
           << ") perm_walk(pk::WalkArgs wa, void *xg_base) {\n";
         o << "    pk::GenPol pol;\n";
         o << "    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;\n";

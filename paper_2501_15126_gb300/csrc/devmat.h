@@ -34,31 +34,35 @@ struct BatchMat {
 };
 
 // Launch arguments of the generic kernels: any number of matrices of one
-// NMAX bucket and one arithmetic, their images packed devmat_stride apart.
+// NMAX bucket and one arithmetic, their images packed in devmats.
 struct BatchArgs {
     const BatchMat *mats;
-    const void *devmats;
+    const void *devmats;                // images; BatchMat::image is an offset in 16-byte units
     unsigned long long ntasks;          // sum of all matrices' tasks
     unsigned long long *task_counter;   // zeroed before the launch
-    unsigned long long *task_out;       // ntasks * words
+    unsigned long long *task_out;       // results, indexed through BatchMat::out_offset
     unsigned long long *skip_counter;   // may be null
-    unsigned long long devmat_stride;   // bytes between consecutive images
+    unsigned long long slot_bytes;      // per-warp shared-memory slot (>= every image's bytes)
     int nmat;
     int zero_skip;
 };
 
-// The ordered matrix as the generic kernels read it (shared memory image).
-// Slots are rows in the plan's order; positions are columns in the plan's
-// order.  V is double (FP64 path) or int (exact path: values doubled).
+// The ordered matrix as the generic kernels read it (a variable-length
+// image; only the first `bytes` bytes exist).  Slots are rows in the plan's
+// order; positions are columns in the plan's order.  Column p's values, in
+// slot order, are val[colptr[p] ..].  V is double (FP64 path) or int (exact
+// path: values doubled).
 template <int NMAX, typename V>
 struct DevMat {
     int n;                              // dimension
     int top;                            // highest nonempty row group
-    int pad0, pad1;
+    int nnz;                            // values stored (columns 0..n-2)
+    int bytes;                          // size of this image, a multiple of 16
     unsigned long long colmask[NMAX];   // slots touched by column position p (p < n-1)
     unsigned long long grpmask[NMAX];   // slots whose first touching column is m
+    unsigned short colptr[NMAX];        // first value of column p
     V x0[NMAX];                         // Nijenhuis-Wilf start values by slot
-    V val[NMAX * NMAX];                 // val[p * NMAX + slot] = value of column p at slot
+    V val[NMAX * NMAX];                 // nnz values, column after column
 };
 
 }  // namespace pk

@@ -17,7 +17,13 @@
 #include "kernels.hpp"
 
 #ifndef PERM_GENERIC_B
-#define PERM_GENERIC_B 4
+#define PERM_GENERIC_B 5
+#endif
+
+// Resident 256-thread blocks per SM the kernels are compiled for (their
+// register budget): 2 -> 128 registers, 3 -> 80.
+#ifndef PERM_GENERIC_MIN_BLOCKS
+#define PERM_GENERIC_MIN_BLOCKS 2
 #endif
 
 namespace pk {
@@ -93,22 +99,22 @@ struct GenericPol {
     template <int J, int S>
     __device__ __forceinline__ void flip(X (&x)[NX]) {
         u64 cm = ((const volatile u64 *)m->colmask)[J];
-        const volatile V *v = m->val + J * NMAX;
+        const volatile V *v = m->val + ((const volatile unsigned short *)m->colptr)[J];
         while (cm) {
             const int i = ctz64(cm);
             cm &= cm - 1;
-            add_slot_s<S>(x, i, v[i]);
+            add_slot_s<S>(x, i, *v++);
         }
     }
     template <int J>
     __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
     __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {
         u64 cm = ((const volatile u64 *)m->colmask)[j];
-        const volatile V *v = m->val + j * NMAX;
+        const volatile V *v = m->val + ((const volatile unsigned short *)m->colptr)[j];
         while (cm) {
             const int i = ctz64(cm);
             cm &= cm - 1;
-            add_slot(x, i, v[i], s);
+            add_slot(x, i, *v++, s);
         }
     }
     __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
@@ -160,11 +166,11 @@ struct GenericPol {
 // warp stages that matrix's image in its own shared-memory slot (restaged
 // only when the matrix changes).
 template <int NMAX, class A>
-__global__ void __launch_bounds__(256) k_walk_generic(BatchArgs ba) {
+__global__ void __launch_bounds__(256, PERM_GENERIC_MIN_BLOCKS) k_walk_generic(BatchArgs ba) {
     typedef DevMat<NMAX, typename A::V> M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    M *slot = reinterpret_cast<M *>(smem_raw + (size_t)warp * sizeof(M));
+    M *slot = reinterpret_cast<M *>(smem_raw + (size_t)warp * ba.slot_bytes);
     int cached = -1;
     u64 skipped = 0;
     for (;;) {
@@ -186,9 +192,10 @@ __global__ void __launch_bounds__(256) k_walk_generic(BatchArgs ba) {
         if (bm.image != cached) {
             __syncwarp();
             const uint4 *src = reinterpret_cast<const uint4 *>(
-                reinterpret_cast<const unsigned char *>(ba.devmats) + (size_t)bm.image * ba.devmat_stride);
+                reinterpret_cast<const unsigned char *>(ba.devmats) + (size_t)bm.image * 16);
+            const int words = reinterpret_cast<const int *>(src)[3] / 16;   // the image's own size
             uint4 *dst = reinterpret_cast<uint4 *>(slot);
-            for (int i = lane; i < (int)(sizeof(M) / 16); i += 32) dst[i] = src[i];
+            for (int i = lane; i < words; i += 32) dst[i] = src[i];
             __syncwarp();
             cached = bm.image;
         }
@@ -221,9 +228,10 @@ __global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typen
             const int p = ctz64(G);
             G &= G - 1;
             const u64 cm = m->colmask[p];
+            int k = m->colptr[p];
 #pragma unroll
             for (int i = 0; i < NMAX; ++i)
-                if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], m->val[p * NMAX + i], 1);
+                if ((cm >> i) & 1ull) x[i] = A::upd_rt(x[i], m->val[k++], 1);
         }
         typename A::P q = A::one();
 #pragma unroll
@@ -253,13 +261,8 @@ __global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typen
 namespace perm {
 
 template <int NMAX, class A>
-static size_t smem_walk_t(int block) {
-    return (size_t)(block / 32) * sizeof(pk::DevMat<NMAX, typename A::V>);
-}
-
-template <int NMAX, class A>
 static cudaError_t launch_walk_t(const pk::BatchArgs &ba, int grid, int block, cudaStream_t st) {
-    const size_t smem = smem_walk_t<NMAX, A>(block);
+    const size_t smem = (size_t)(block / 32) * ba.slot_bytes;
     cudaError_t e = cudaFuncSetAttribute(pk::k_walk_generic<NMAX, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -282,8 +285,8 @@ static cudaError_t attr_walk_t(cudaFuncAttributes *attr) {
 }
 
 template <int NMAX, class A>
-static cudaError_t occ_walk_t(int block, int *blocks_per_sm) {
-    const size_t smem = smem_walk_t<NMAX, A>(block);
+static cudaError_t occ_walk_t(int block, size_t slot_bytes, int *blocks_per_sm) {
+    const size_t smem = (size_t)(block / 32) * slot_bytes;
     cudaError_t e = cudaFuncSetAttribute(pk::k_walk_generic<NMAX, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -298,7 +301,7 @@ static GenericFns make_fns() {
     f.attr = attr_walk_t<NMAX, A>;
     f.occ = occ_walk_t<NMAX, A>;
     f.block_log2 = PERM_GENERIC_B;
-    f.devmat_bytes = sizeof(pk::DevMat<NMAX, typename A::V>);
+    f.devmat_bytes = sizeof(pk::DevMat<NMAX, typename A::V>);   // capacity of a dense image
     return f;
 }
 

@@ -15,9 +15,9 @@ struct GenericFns {
     cudaError_t (*direct)(const void *devmat, uint64_t g_lo, uint64_t g_hi, uint64_t *block_out, int grid, int block,
                           cudaStream_t st) = nullptr;
     cudaError_t (*attr)(cudaFuncAttributes *attr) = nullptr;
-    cudaError_t (*occ)(int block, int *blocks_per_sm) = nullptr;
+    cudaError_t (*occ)(int block, size_t slot_bytes, int *blocks_per_sm) = nullptr;
     int block_log2 = 0;   // B of this family: 2^B steps unrolled per block
-    size_t devmat_bytes = 0;
+    size_t devmat_bytes = 0;   // the largest possible image (every value stored)
 };
 
 // arith: 0 = FP64, 1..3 = exact modulo 2^(64 arith).  nmax in {16, 32, 48}.

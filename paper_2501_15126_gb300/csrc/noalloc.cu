@@ -89,7 +89,7 @@ extern "C" perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm
     P.nmax = nmax;
     P.gf = generic_fns(nmax, P.arith);
     if (!P.gf.walk) { out->status = PERM_ERR_INTERNAL; return fail(PERM_ERR_INTERNAL, "no generic kernel"); }
-    const size_t img_bytes = devmat_bytes(P.arith, nmax);
+    const size_t img_bytes = devmat_bytes_for(P.L, P.arith, nmax);
     if (img_bytes > kOffTasks - kOffImage) { out->status = PERM_ERR_INTERNAL; return fail(PERM_ERR_INTERNAL, "image too large"); }
     const uint64_t max_tasks = (kNoAllocScratchBytes - kOffTasks) / (8ull * P.words);
     cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
@@ -109,7 +109,7 @@ extern "C" perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm
         P.ntasks = (uint64_t)P.grid;
     } else {
         int bps = 0;
-        if ((e = P.gf.occ(256, &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
+        if ((e = P.gf.occ(256, img_bytes, &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
         st = choose_launch(P, P.gf.block_log2, bps > 0 ? bps : 1, 256);
         // raise the chunk length until the task results fit the scratch array
         while (st == PERM_OK && P.ntasks > max_tasks) {
@@ -146,7 +146,7 @@ extern "C" perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm
         ba.task_counter = reinterpret_cast<unsigned long long *>(d_counters);
         ba.task_out = reinterpret_cast<unsigned long long *>(d_tasks);
         ba.skip_counter = reinterpret_cast<unsigned long long *>(d_counters + 1);
-        ba.devmat_stride = P.gf.devmat_bytes;
+        ba.slot_bytes = img_bytes;
         ba.nmat = 1;
         ba.zero_skip = P.opts.zero_skip ? 0 : 1;
         if ((e = P.gf.walk(ba, P.grid, P.block, st_)) != cudaSuccess) return cuda_fail(e, "walk kernel launch");

@@ -25,6 +25,7 @@ struct perm_plan_s {
     double ops_per_step = 0.0, ops_per_step_paper = 0.0;
     double ms_plan = 0.0, ms_compile = 0.0;
     int engine = 0, nmax = 0, words = 2;
+    size_t img_bytes = 0;     // generic kernels: size of the matrix image
     int K = 0, grid = 1, block = 256, regs = 0;
     int k = 0, c = 0;         // Algorithm 4 split (codegen)
     uint64_t chunk_lo = 0, chunk_hi = 0, ntasks = 0;
@@ -62,7 +63,8 @@ void describe(const perm_plan_s &P, perm_result_t *out);
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);
 int nmax_bucket(int n);
 void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img);
-size_t devmat_bytes(int arith, int nmax);
+size_t devmat_bytes(int arith, int nmax, int nnz);
+size_t devmat_bytes_for(const Layout &L, int arith, int nmax);
 void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, unsigned char *dst);
 perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block);
 

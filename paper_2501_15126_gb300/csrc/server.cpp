@@ -49,6 +49,11 @@ namespace {
 
 constexpr int kStreams = 2;
 constexpr uint64_t kSmallShare = 64;          // tasks every active request gets per wave
+constexpr double kWaveSteps = 268435456.0;    // Gray steps per wave (2^28, a few ms): short waves let
+                                              // requests that arrive meanwhile start soon
+constexpr int kServeChunkLog2 = 12;           // chunk length target: tasks of 2^17 steps fill short waves
+constexpr int kAdmitScan = 256;               // queued requests looked at past a blocked one
+constexpr double kNoSkipAfterMs = 200.0;      // a request blocked this long stops being overtaken
 constexpr size_t kQueueMax = 1 << 20;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -60,6 +65,7 @@ struct Request {
     int slot = -1;
     uint64_t ntasks = 0, next_task = 0, done_tasks = 0;
     uint64_t out_offset = 0;    // first task of the request's result range in the family pool
+    size_t img_bytes = 0;       // size of the request's matrix image
     double t_submit = 0.0;
     int inflight_waves = 0;
     bool failed = false;
@@ -198,7 +204,7 @@ struct perm_server_s {
         if (!F.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this family");
         F.K_target = tuned_chunk_log2(nmax, arith);
         int bps = 0;
-        cudaError_t e = F.gf.occ(256, &bps);
+        cudaError_t e = F.gf.occ(256, F.gf.devmat_bytes, &bps);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
         F.grid_max = kSMCount * std::max(bps, 1);
         const int slots = opts.max_inflight;
@@ -253,41 +259,59 @@ struct perm_server_s {
     }
 
     // Admits queued requests while budget, slots and pool space allow.
+    // Tries to admit one queued request; false when it does not fit now.
+    bool try_admit(Request *r) {
+        perm_plan_s &P = *r->P;
+        const double steps = (double)P.total;
+        if (!active.empty() && steps_active + steps > step_budget) return false;
+        if (r->family >= 0) {
+            Family &F = fam[r->family];
+            if (F.free_slots.empty()) return false;
+            // at most 2^20 tasks per request, so the largest n fits the result pool
+            const int K = batch_chunk_log2(P.m.n, F.gf.block_log2, std::max(kServeChunkLog2, P.m.n - 26));
+            const uint64_t chunks = P.total >> K;
+            const uint64_t ntasks = (chunks + 31) / 32;
+            uint64_t off = 0;
+            if (!F.ranges.alloc(ntasks, &off)) return false;
+            r->slot = F.free_slots.back();
+            F.free_slots.pop_back();
+            P.K = K;
+            P.chunk_lo = 0;
+            P.chunk_hi = chunks;
+            P.ntasks = ntasks;
+            P.engine = PERM_ENGINE_GENERIC;
+            P.gf = F.gf;
+            P.nmax = F.nmax;
+            r->ntasks = ntasks;
+            r->out_offset = off;
+            // the image goes up on stream 0 before any wave that reads it
+            std::vector<unsigned char> img;
+            build_devmat(P.m, P.L, F.arith, F.nmax, img);
+            r->img_bytes = img.size();
+            cudaMemcpyAsync(F.d_images + (size_t)r->slot * F.gf.devmat_bytes, img.data(), img.size(),
+                            cudaMemcpyHostToDevice, streams[0]);
+        }
+        steps_active += steps;
+        active.push_back(r);
+        return true;
+    }
+
+    // Admits queued requests in arrival order while budget, slots and pool
+    // space allow.  A request that does not fit may be overtaken by later,
+    // smaller ones (up to kAdmitScan of them), until it has waited
+    // kNoSkipAfterMs; then everything behind it waits too.
     void admit() {
-        while (!queue.empty()) {
-            Request *r = queue.front();
-            perm_plan_s &P = *r->P;
-            const double steps = (double)P.total;
-            if (!active.empty() && steps_active + steps > step_budget) break;
-            if (r->family >= 0) {
-                Family &F = fam[r->family];
-                if (F.free_slots.empty()) break;
-                // at most 2^20 tasks per request, so the largest n fits the result pool
-                const int K = batch_chunk_log2(P.m.n, F.gf.block_log2, std::max(F.K_target, P.m.n - 26));
-                const uint64_t chunks = P.total >> K;
-                const uint64_t ntasks = (chunks + 31) / 32;
-                uint64_t off = 0;
-                if (!F.ranges.alloc(ntasks, &off)) break;
-                r->slot = F.free_slots.back();
-                F.free_slots.pop_back();
-                P.K = K;
-                P.chunk_lo = 0;
-                P.chunk_hi = chunks;
-                P.ntasks = ntasks;
-                P.engine = PERM_ENGINE_GENERIC;
-                P.gf = F.gf;
-                P.nmax = F.nmax;
-                r->ntasks = ntasks;
-                r->out_offset = off;
-                // the image goes up on stream 0 before any wave that reads it
-                std::vector<unsigned char> img;
-                build_devmat(P.m, P.L, F.arith, F.nmax, img);
-                cudaMemcpyAsync(F.d_images + (size_t)r->slot * F.gf.devmat_bytes, img.data(), img.size(),
-                                cudaMemcpyHostToDevice, streams[0]);
+        const double t = now_ms();
+        int scanned = 0;
+        for (auto it = queue.begin(); it != queue.end() && scanned < kAdmitScan;) {
+            Request *r = *it;
+            if (try_admit(r)) {
+                it = queue.erase(it);
+                continue;
             }
-            queue.pop_front();
-            steps_active += steps;
-            active.push_back(r);
+            if (t - r->t_submit > kNoSkipAfterMs) break;
+            ++it;
+            ++scanned;
         }
     }
 
@@ -317,21 +341,20 @@ struct perm_server_s {
         for (Wave &c : waves)
             if (!c.busy) { w = &c; break; }
         if (!w) return false;
-        const uint64_t wave_tasks = (uint64_t)F.grid_max * 8 * 2;   // two rounds of every resident warp
         std::vector<Part> parts;
         std::unordered_map<Request *, size_t> where;
-        uint64_t budget = wave_tasks;
+        double budget = kWaveSteps;
         const int maxent = opts.max_inflight * 2;
         // pass 1: a small share for everyone; pass 2: the rest to the oldest.
         // A request's two shares are contiguous, so they merge into one slice.
-        for (int pass = 0; pass < 2 && budget; ++pass) {
+        for (int pass = 0; pass < 2 && budget > 0; ++pass) {
             for (Request *r : active) {
                 if (r->family != fi || r->failed) continue;
                 const uint64_t left = r->ntasks - r->next_task;
                 if (!left) continue;
+                const double task_steps = std::ldexp(32.0, r->P->K);
                 uint64_t take = pass == 0 ? std::min(left, kSmallShare) : left;
-                take = std::min(take, budget);
-                if (!take) break;
+                take = std::min<uint64_t>(take, std::max<uint64_t>(1, (uint64_t)(budget / task_steps)));
                 auto it = where.find(r);
                 if (it != where.end()) {
                     parts[it->second].count += take;
@@ -341,8 +364,8 @@ struct perm_server_s {
                     parts.push_back(Part{r, r->next_task, take});
                 }
                 r->next_task += take;
-                budget -= take;
-                if (!budget) break;
+                budget -= (double)take * task_steps;
+                if (budget <= 0) break;
             }
         }
         if (parts.empty()) return false;
@@ -357,7 +380,7 @@ struct perm_server_s {
             bm.chunk_lo = first * 32;
             bm.chunk_hi = std::min<uint64_t>((first + take) * 32, r->P->chunk_hi);
             bm.out_offset = r->out_offset + first;
-            bm.image = r->slot;
+            bm.image = (int)((size_t)r->slot * F.gf.devmat_bytes / 16);
             bm.K = r->P->K;
             r->inflight_waves += 1;
             t += take;
@@ -375,10 +398,15 @@ struct perm_server_s {
         ba.task_counter = reinterpret_cast<unsigned long long *>(w->d_counters);
         ba.task_out = reinterpret_cast<unsigned long long *>(F.d_pool);
         ba.skip_counter = nullptr;
-        ba.devmat_stride = F.gf.devmat_bytes;
+        size_t slot_bytes = 16;
+        for (const Part &pt : w->parts) slot_bytes = std::max(slot_bytes, pt.req->img_bytes);
+        ba.slot_bytes = slot_bytes;
         ba.nmat = (int)w->parts.size();
         ba.zero_skip = 1;
-        const int grid = (int)std::min<uint64_t>((uint64_t)F.grid_max, (t * 32 + 255) / 256);
+        int bps = 1;
+        F.gf.occ(256, slot_bytes, &bps);
+        const uint64_t grid_occ = (uint64_t)kSMCount * std::max(bps, 1);
+        const int grid = (int)std::min<uint64_t>(grid_occ, (t * 32 + 255) / 256);
         F.gf.walk(ba, std::max(grid, 1), 256, st);
         cudaEventRecord(w->done, st);
         w->busy = true;
