@@ -99,7 +99,8 @@ enum {
 
 /* Option flags. */
 enum {
-    PERM_FLAG_NO_KERNEL_CACHE = 1   /* codegen: compile even if this source was compiled before */
+    PERM_FLAG_NO_KERNEL_CACHE = 1,  /* codegen: compile even if this source was compiled before */
+    PERM_FLAG_NO_GRAPH = 2          /* perm_compute: never replay the plan as a CUDA graph     */
 };
 
 /* Options; a zeroed struct (or NULL) means "choose automatically". */
@@ -119,6 +120,10 @@ typedef struct {
     uint64_t g_lo, g_hi;   /* Gray-index sub-range [g_lo, g_hi); both 0 = whole range.     */
                            /*   Both ends must be multiples of 32.  A sub-range result is  */
                            /*   the raw partial sum (see perm_result_t).                   */
+    int32_t timeout_ms;    /* device-side deadline for one compute: warps stop taking work */
+                           /*   once the GPU clock passes it, and the call returns         */
+                           /*   PERM_ERR_TIMEOUT (the context stays usable); 0 = none      */
+    int32_t reserved1;
 } perm_opts_t;
 
 /* Result of one permanent (or one Gray sub-range). */
@@ -162,7 +167,10 @@ perm_status_t perm_plan_create(const perm_matrix_t *A, const perm_opts_t *opts, 
 
 /* Runs the Gray-code walk of a plan on `stream` and fills *out.  The plan's
    device buffers are reused; two perm_compute calls on one plan must not
-   overlap.  Errors: ARG, CUDA, INTERNAL. */
+   overlap.  From the second call on, the plan's launches (workspace reset,
+   walk, reduction, result copy) are captured once into a CUDA graph and
+   replayed with one launch (unless PERM_FLAG_NO_GRAPH).
+   Errors: ARG, CUDA, INTERNAL. */
 perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out);
 
 /* Frees a plan (NULL is allowed). */
@@ -196,6 +204,19 @@ perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm_opts_t *op
    (the plain one-launch-per-matrix form, for comparison). */
 perm_status_t perm_batch_sequential(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
                                     void *stream, perm_result_t *out);
+
+/* Resumable run (the sub-range form of Sec. II-A): walks A in aligned Gray
+   slices of 2^slice_log2 indices and appends each finished slice's partial
+   sum to the text file `path` (created if absent).  Slices already recorded
+   are skipped, so a stopped run resumes where it left off.  At most
+   max_slices new slices are computed per call (0 = all).  Returns OK with the
+   permanent in *out once every slice is recorded (combined in slice order:
+   the same bits however the run was split), or NOT_READY with out->steps =
+   Gray indices recorded so far.  The file names the matrix (hash of values
+   and order), the arithmetic and the slice size; a file written for another
+   run gives ARG.  slice_log2 in [5, n-1]. */
+perm_status_t perm_checkpoint_run(const perm_matrix_t *A, const perm_opts_t *opts, const char *path,
+                                  int32_t slice_log2, int32_t max_slices, void *stream, perm_result_t *out);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -22,6 +22,7 @@ PERM_CSR, PERM_CSC = 0, 1
 PERM_ORDER_AUTO, PERM_ORDER_NONE, PERM_ORDER_DEGREE, PERM_ORDER_PAPER = 0, 1, 2, 3
 PERM_ENGINE_AUTO, PERM_ENGINE_GENERIC, PERM_ENGINE_CODEGEN = 0, 1, 2
 PERM_FLAG_NO_KERNEL_CACHE = 1
+PERM_FLAG_NO_GRAPH = 2
 
 c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 
@@ -34,7 +35,7 @@ class Matrix(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("ordering", c_i32), ("engine", c_i32), ("reg_rows", c_i32), ("chunk_log2", c_i32),
                 ("threads", c_i32), ("exact_words", c_i32), ("zero_skip", c_i32), ("flags", c_i32),
-                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64)]
+                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64), ("timeout_ms", c_i32), ("reserved1", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -106,6 +107,8 @@ SIGNATURES = [
     ("perm_sizeof", c_i64, [c_i32]),
     ("perm_issue_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     ("perm_compute_noalloc", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), c_vp, ctypes.POINTER(Result)]),
+    ("perm_checkpoint_run", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), ctypes.c_char_p, c_i32, c_i32, c_vp,
+                                    ctypes.POINTER(Result)]),
 ]
 
 _lib = None
@@ -211,6 +214,18 @@ def permanent_noalloc(a, stream: int = 0, **kw) -> Result:
     check(lib().perm_compute_noalloc(ctypes.byref(m.c), ctypes.byref(o), c_vp(stream), ctypes.byref(r)),
           "perm_compute_noalloc")
     return r
+
+
+def checkpoint_run(a, path: str, slice_log2: int, max_slices: int = 0, stream: int = 0, **kw):
+    """perm_checkpoint_run: (status, Result); status is PERM_OK or PERM_ERR_NOT_READY."""
+    m = a if isinstance(a, CSRMatrix) else CSRMatrix(a)
+    o = opts(**kw)
+    r = Result()
+    st = lib().perm_checkpoint_run(ctypes.byref(m.c), ctypes.byref(o), path.encode(), slice_log2, max_slices,
+                                   c_vp(stream), ctypes.byref(r))
+    if st not in (PERM_OK, PERM_ERR_NOT_READY):
+        check(st, "perm_checkpoint_run")
+    return st, r
 
 
 def inspect(a, **kw) -> Inspect:

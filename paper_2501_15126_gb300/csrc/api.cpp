@@ -164,6 +164,7 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     if (opts.exact_words < 0 || opts.exact_words > 3) return fail(PERM_ERR_ARG, "exact_words must be 0..3");
     if (opts.chunk_log2 < 0 || opts.chunk_log2 > 63) return fail(PERM_ERR_ARG, "bad chunk_log2");
     if (opts.threads < 0) return fail(PERM_ERR_ARG, "threads < 0");
+    if (opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
     P.zero = !has_perfect_matching(P.m);
     P.L = choose_layout(P.m, opts.ordering);
     P.ops_per_step = cost_per_step(P.L, false);
@@ -202,7 +203,7 @@ perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, i
     if (!K) {
         // enough 32-chunk tasks for every resident warp several times over, but
         // chunks of at least 2^(B+3) steps so the start vector stays a small cost
-        const double want_tasks = 8.0 * (double)resident_warps;
+        const double want_tasks = 64.0 * (double)resident_warps;   // keeps the last round of tasks short
         K = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * want_tasks)));
         K = std::max(K, block_log2 + 3);
     }
@@ -320,12 +321,14 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
     return PERM_OK;
 }
 
-// Launches the walk and the reduction; no synchronisation.
-perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st) {
+// Launches the walk and the reduction; no synchronisation.  With
+// record_events false (graph capture) the timing events are left out: a
+// replayed graph is timed by events around its launch instead.
+perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(P.d_ws, 0, 8 * 8, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     uint64_t *task_out = P.d_ws + kWsTaskOut;
-    if ((e = cudaEventRecord(P.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if (record_events && (e = cudaEventRecord(P.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if (P.direct) {
         e = P.gf.direct(P.d_devmat, P.g_lo, P.g_hi, task_out, P.grid, P.block, st);
         if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
@@ -340,6 +343,9 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st) {
         ba.slot_bytes = P.img_bytes;
         ba.nmat = 1;
         ba.zero_skip = P.opts.zero_skip ? 0 : 1;
+        ba.timeout_ns = (unsigned long long)std::max(0, P.opts.timeout_ms) * 1000000ull;
+        ba.deadline_word = reinterpret_cast<unsigned long long *>(P.d_ws + kWsDeadline);
+        ba.abort_flag = reinterpret_cast<unsigned int *>(P.d_ws + kWsAbort);
         e = P.gf.walk(ba, P.grid, P.block, st);
         if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     } else {
@@ -352,12 +358,15 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st) {
         wa.skip_counter = reinterpret_cast<unsigned long long *>(P.d_ws + 1);
         wa.K = P.K;
         wa.zero_skip = P.opts.zero_skip ? 0 : 1;
+        wa.timeout_ns = (unsigned long long)std::max(0, P.opts.timeout_ms) * 1000000ull;
+        wa.deadline_word = reinterpret_cast<unsigned long long *>(P.d_ws + kWsDeadline);
+        wa.abort_flag = reinterpret_cast<unsigned int *>(P.d_ws + kWsAbort);
         e = codegen_launch(P, wa, st);
         if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     }
     if ((e = reduce_launch(P.arith, task_out, P.ntasks, P.d_ws + 2, st)) != cudaSuccess)
         return cuda_fail(e, "reduce kernel launch");
-    if ((e = cudaEventRecord(P.ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    if (record_events && (e = cudaEventRecord(P.ev1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if ((e = cudaMemcpyAsync(P.h_res, P.d_ws, 8 * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(result)");
     return PERM_OK;
@@ -435,6 +444,10 @@ perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, P.ev0, P.ev1);
     out->ms_kernel = ms;
+    if (P.h_res[kWsAbort]) {
+        out->status = PERM_ERR_TIMEOUT;
+        return fail(PERM_ERR_TIMEOUT, "device-side deadline passed; the walk stopped early");
+    }
     const uint64_t skipped = P.h_res[1];
     const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
     const uint64_t blocks = (P.g_hi - P.g_lo) >> std::max(1, B);
@@ -451,6 +464,8 @@ perm_plan_s::~perm_plan_s() {
     if (h_res) cudaFreeHost(h_res);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     perm::codegen_release(*this);
 }
 
@@ -470,14 +485,43 @@ perm_status_t perm_plan_create(const perm_matrix_t *A, const perm_opts_t *opts, 
     return PERM_OK;
 }
 
+// Captures the plan's launches into a CUDA graph (on a plan-owned stream).
+static bool capture_graph(perm_plan_s &P) {
+    if (!P.cap_stream && cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(P.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const perm_status_t s = plan_launch(P, P.cap_stream, false);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(P.cap_stream, &g);
+    if (s != PERM_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&P.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { P.graph = nullptr; cudaGetLastError(); return false; }
+    return true;
+}
+
 perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out) {
     if (!plan || !out) return fail(PERM_ERR_ARG, "NULL plan or result");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!plan->zero) {
-        perm_status_t s = plan_launch(*plan, st);
+        const bool use_graph = !(plan->opts.flags & PERM_FLAG_NO_GRAPH) && plan->computes >= 1;
+        if (use_graph && !plan->graph && !plan->graph_failed) plan->graph_failed = !capture_graph(*plan);
+        perm_status_t s = PERM_OK;
+        if (use_graph && plan->graph) {
+            cudaEventRecord(plan->ev0, st);
+            const cudaError_t e = cudaGraphLaunch(plan->graph, st);
+            if (e != cudaSuccess) s = cuda_fail(e, "cudaGraphLaunch");
+            cudaEventRecord(plan->ev1, st);
+        } else {
+            s = plan_launch(*plan, st);
+        }
         if (s != PERM_OK) { std::memset(out, 0, sizeof(*out)); out->status = s; return s; }
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { out->status = PERM_ERR_CUDA; return cuda_fail(e, "cudaStreamSynchronize"); }
+        plan->computes += 1;
     }
     return plan_finish(*plan, out);
 }

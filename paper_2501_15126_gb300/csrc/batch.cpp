@@ -113,7 +113,7 @@ int BatchGroup::upload(cudaStream_t st) {
 
 int BatchGroup::launch(cudaStream_t st, int zero_skip) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(d_counters, 0, 16, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if ((e = cudaMemsetAsync(d_counters, 0, 32, st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     pk::BatchArgs ba;
     ba.mats = d_mats;
     ba.devmats = d_images;
@@ -124,6 +124,9 @@ int BatchGroup::launch(cudaStream_t st, int zero_skip) {
     ba.slot_bytes = slot_bytes;
     ba.nmat = (int)mats.size();
     ba.zero_skip = zero_skip;
+    ba.timeout_ns = timeout_ns;
+    ba.deadline_word = reinterpret_cast<unsigned long long *>(d_counters + 2);
+    ba.abort_flag = reinterpret_cast<unsigned int *>(d_counters + 3);
     if ((e = gf.walk(ba, grid, block, st)) != cudaSuccess) return cuda_fail(e, "batch walk launch");
     if ((e = batch_reduce_launch(arith, d_mats, (int)mats.size(), ntasks, d_task_out, d_result, st)) != cudaSuccess)
         return cuda_fail(e, "batch reduce launch");
@@ -182,10 +185,20 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
     const double t_prep = now_ms() - t0;
 
     // one arena for every group
+    if (opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
     size_t total = 0;
     for (auto &kv : groups) {
         BatchGroup &G = kv.second;
-        const int K_target = opts.chunk_log2 ? opts.chunk_log2 : tuned_chunk_log2(kv.first.first, kv.first.second);
+        G.timeout_ns = (unsigned long long)std::max(0, opts.timeout_ms) * 1000000ull;
+        int K_target = opts.chunk_log2;
+        if (!K_target) {
+            if (!chunk_log2_is_tuned(kv.first.first, kv.first.second)) {
+                G.nmax = kv.first.first;
+                G.arith = kv.first.second;
+                autotune_group(G, st);
+            }
+            K_target = tuned_chunk_log2(kv.first.first, kv.first.second);
+        }
         perm_status_t s = (perm_status_t)G.setup(kv.first.first, kv.first.second, K_target);
         if (s != PERM_OK) return s;
         total += G.arena_bytes();
@@ -215,9 +228,9 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
     raw.reserve(groups.size());
     for (auto &kv : groups) {
         BatchGroup &G = kv.second;
-        raw.emplace_back(G.mats.size() * (size_t)G.words + 2);
+        raw.emplace_back(G.mats.size() * (size_t)G.words + 4);
         cudaMemcpyAsync(raw.back().data(), G.d_result, G.mats.size() * (size_t)G.words * 8, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(raw.back().data() + G.mats.size() * (size_t)G.words, G.d_counters, 16,
+        cudaMemcpyAsync(raw.back().data() + G.mats.size() * (size_t)G.words, G.d_counters, 32,
                         cudaMemcpyDeviceToHost, st);
     }
     cudaError_t e = cudaStreamSynchronize(st);
@@ -227,8 +240,11 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(batch)");
     size_t gi = 0;
+    bool timed_out = false;
     for (auto &kv : groups) {
         BatchGroup &G = kv.second;
+        const bool aborted = raw[gi][G.mats.size() * (size_t)G.words + 3] != 0;
+        timed_out |= aborted;
         for (size_t j = 0; j < G.idx.size(); ++j) {
             const int i = G.idx[j];
             perm_plan_s &P = *plans[i];
@@ -238,10 +254,12 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
             describe(P, &out[i]);
             out[i].ms_kernel = ms;
             out[i].ms_plan = t_prep / count;
-            finish_raw(P, raw[gi].data() + j * (size_t)G.words, &out[i]);
+            if (aborted) out[i].status = PERM_ERR_TIMEOUT;
+            else finish_raw(P, raw[gi].data() + j * (size_t)G.words, &out[i]);
         }
         ++gi;
     }
+    if (timed_out) fail(PERM_ERR_TIMEOUT, "device-side deadline passed in a batch walk");
     for (int i : singles) {
         perm_plan_s &P = *plans[i];
         perm_status_t s = plan_device_setup(P);

@@ -19,6 +19,9 @@ int batch_chunk_log2(int n, int B, int K_target);
 
 // The autotuned chunk target of a (NMAX, arithmetic) family (tune.cpp).
 int tuned_chunk_log2(int nmax, int arith);
+bool chunk_log2_is_tuned(int nmax, int arith);
+struct BatchGroup;
+int autotune_group(const BatchGroup &group, cudaStream_t st);
 
 // Matrices of one NMAX bucket and one arithmetic: one launch.
 struct BatchGroup {
@@ -30,6 +33,7 @@ struct BatchGroup {
     std::vector<unsigned char> images;
     uint64_t ntasks = 0;
     size_t slot_bytes = 16;                // the largest image of the group
+    unsigned long long timeout_ns = 0;     // device-side deadline (0 = none)
     int grid = 1, block = 256, regs = 0;
     unsigned char *d_images = nullptr;
     pk::BatchMat *d_mats = nullptr;

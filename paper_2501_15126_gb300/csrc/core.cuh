@@ -56,6 +56,30 @@ namespace pk {
 
 __device__ __forceinline__ int ctz64(u64 v) { return __ffsll((long long)v) - 1; }
 
+// Nanoseconds from the GPU's global timer.
+__device__ __forceinline__ u64 global_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-side deadline.  The first warp to fetch a task stores "now +
+// timeout" in *deadline_word; every warp compares the GPU clock with it
+// before taking a task, and past it raises the abort flag and stops taking
+// work.  Nothing ever waits on the flag or the word.
+__device__ __forceinline__ bool past_deadline(u64 timeout_ns, u64 *deadline_word, unsigned int *abort_flag) {
+    if (!timeout_ns) return false;
+    const u64 now = global_ns();
+    u64 d = *(volatile u64 *)deadline_word;
+    if (!d) {
+        atomicCAS(deadline_word, 0ull, now + timeout_ns);
+        d = *(volatile u64 *)deadline_word;
+    }
+    if (now < d) return false;
+    atomicExch(abort_flag, 1u);
+    return true;
+}
+
 // ------------------------------------------------------------------ FP64 arithmetic
 
 struct ArithF64 {
@@ -72,6 +96,7 @@ struct ArithF64 {
     typedef double Blk;
     static __device__ __forceinline__ Blk blk_zero() { return 0.0; }
     template <int S> static __device__ __forceinline__ void blk_add(Blk &b, P p) { if (S > 0) b += p; else b -= p; }
+    static __device__ __forceinline__ void blk_accumulate(Blk &a, Blk b) { a += b; }
     static __device__ __forceinline__ Acc acc_zero() { Acc a; a.hi = 0.0; a.lo = 0.0; return a; }
     // TwoSum (Knuth): a.hi + b = s + e exactly
     static __device__ __forceinline__ void acc_merge(Acc &a, Blk b) {
@@ -220,6 +245,7 @@ struct ArithExact {
     template <int S> static __device__ __forceinline__ void blk_add(Blk &b, const P &p) {
         if (S > 0) ring_add<L>(b, p); else ring_sub<L>(b, p);
     }
+    static __device__ __forceinline__ void blk_accumulate(Blk &a, const Blk &b) { ring_add<L>(a, b); }
     static __device__ __forceinline__ Acc acc_zero() { return blk_zero(); }
     static __device__ __forceinline__ void acc_merge(Acc &a, const Blk &b) { ring_add<L>(a, b); }
     static __device__ __forceinline__ Acc acc_add(Acc a, const Acc &b) { ring_add<L>(a, b); return a; }
@@ -343,8 +369,15 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
     pol.init_x(x, g0 ^ (g0 >> 1));
     P QB = pol.chain_init(x);
     typename A::Acc acc = A::acc_zero();
+    // block sums go into a plain mid-level sum, merged into the compensated
+    // accumulator every 8 blocks (and at the end of the chunk)
+    typename A::Blk mid = A::blk_zero();
     const u64 nblocks = 1ull << (K - Bv);
     for (u64 h = 0; h < nblocks; ++h) {
+        if (h != 0 && (h & 7) == 0) {
+            A::acc_merge(acc, mid);
+            mid = A::blk_zero();
+        }
         const u64 gb = g0 + (h << Bv);
         if (h != 0) {
             const int j = Bv + ctz64(h);
@@ -379,8 +412,9 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
             A::template blk_add<1>(blk, pol.template grp<0>(x, Q[1]));
             BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
         }
-        A::acc_merge(acc, blk);
+        A::blk_accumulate(mid, blk);
     }
+    A::acc_merge(acc, mid);
     return acc;
 }
 
@@ -392,7 +426,7 @@ __device__ __forceinline__ void walk_tasks(Pol &pol, const WalkArgs &wa) {
     u64 skipped = 0;
     for (;;) {
         u64 task = 0;
-        if (lane == 0) task = atomicAdd(wa.task_counter, 1ull);
+        if (lane == 0) task = past_deadline(wa.timeout_ns, wa.deadline_word, wa.abort_flag) ? ~0ull : atomicAdd(wa.task_counter, 1ull);
         task = __shfl_sync(PERM_FULLMASK, task, 0);
         if (task >= wa.ntasks) break;
         u64 q = wa.chunk_lo + task * 32ull + (u64)lane;

@@ -16,6 +16,9 @@ struct WalkArgs {
     unsigned long long *skip_counter;   // blocks skipped as all-zero (may be null)
     int K;                              // log2 of the chunk length (>= B)
     int zero_skip;                      // 1 = skip all-zero blocks
+    unsigned long long timeout_ns;      // device-side deadline, counted from the first task fetch (0 = none)
+    unsigned long long *deadline_word;  // zeroed before the launch; the first warp stores its deadline
+    unsigned int *abort_flag;           // set to 1 by a warp that stopped at the deadline
 };
 
 // One entry of a generic (multi-matrix) walk: the launch's tasks
@@ -45,6 +48,9 @@ struct BatchArgs {
     unsigned long long slot_bytes;      // per-warp shared-memory slot (>= every image's bytes)
     int nmat;
     int zero_skip;
+    unsigned long long timeout_ns;      // device-side deadline, counted from the first task fetch (0 = none)
+    unsigned long long *deadline_word;  // zeroed before the launch; the first warp stores its deadline
+    unsigned int *abort_flag;           // set to 1 by a warp that stopped at the deadline
 };
 
 // The ordered matrix as the generic kernels read it (a variable-length

@@ -1,6 +1,5 @@
 // generic_e1.cu -- generic kernels for one arithmetic (see generic_impl.cuh).
 #define PERM_GENERIC_B 5
-#define PERM_GENERIC_MIN_BLOCKS 3
 #include "generic_impl.cuh"
 
 PERM_GENERIC_UNIT(e1, pk::ArithExact<1>)

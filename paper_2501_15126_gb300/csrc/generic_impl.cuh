@@ -166,16 +166,15 @@ struct GenericPol {
 // warp stages that matrix's image in its own shared-memory slot (restaged
 // only when the matrix changes).
 template <int NMAX, class A>
-__global__ void __launch_bounds__(256, PERM_GENERIC_MIN_BLOCKS) k_walk_generic(BatchArgs ba) {
+__device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned char *slot_raw) {
     typedef DevMat<NMAX, typename A::V> M;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    M *slot = reinterpret_cast<M *>(smem_raw + (size_t)warp * ba.slot_bytes);
+    const int lane = threadIdx.x & 31;
+    M *slot = reinterpret_cast<M *>(slot_raw);
     int cached = -1;
     u64 skipped = 0;
     for (;;) {
         u64 task = 0;
-        if (lane == 0) task = atomicAdd(ba.task_counter, 1ull);
+        if (lane == 0) task = past_deadline(ba.timeout_ns, ba.deadline_word, ba.abort_flag) ? ~0ull : atomicAdd(ba.task_counter, 1ull);
         task = __shfl_sync(PERM_FULLMASK, task, 0);
         if (task >= ba.ntasks) break;
         int m = 0;
@@ -210,6 +209,13 @@ __global__ void __launch_bounds__(256, PERM_GENERIC_MIN_BLOCKS) k_walk_generic(B
         if (lane == 0) A::acc_store(ba.task_out + (bm.out_offset + (task - bm.task_begin)) * (u64)A::ACC_WORDS, acc);
     }
     if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
+}
+
+template <int NMAX, class A>
+__global__ void __launch_bounds__(256, PERM_GENERIC_MIN_BLOCKS) k_walk_generic(BatchArgs ba) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    generic_task_loop<NMAX, A>(ba, smem_raw + (size_t)warp * ba.slot_bytes);
 }
 
 // Tiny matrices: one thread per Gray index, x built from scratch.

@@ -149,6 +149,9 @@ extern "C" perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm
         ba.slot_bytes = img_bytes;
         ba.nmat = 1;
         ba.zero_skip = P.opts.zero_skip ? 0 : 1;
+        ba.timeout_ns = 0;
+        ba.deadline_word = nullptr;
+        ba.abort_flag = nullptr;
         if ((e = P.gf.walk(ba, P.grid, P.block, st_)) != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     }
     if ((e = reduce_launch(P.arith, reinterpret_cast<const uint64_t *>(d_tasks), P.ntasks, d_result, st_)) !=

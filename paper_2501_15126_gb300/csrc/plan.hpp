@@ -36,6 +36,10 @@ struct perm_plan_s {
     void *d_xglob = nullptr;    // codegen: rows of x kept in global memory
     uint64_t *h_res = nullptr;  // pinned copy of d_ws[0..7]
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int computes = 0;                      // perm_compute calls so far
+    cudaStream_t cap_stream = nullptr;     // stream the graph is captured on
+    cudaGraphExec_t graph = nullptr;       // the captured launches (second call on)
+    bool graph_failed = false;
     uint64_t len() const { return g_hi - g_lo; }
     ~perm_plan_s();
 };
@@ -43,7 +47,11 @@ struct perm_plan_s {
 namespace perm {
 
 // Workspace layout (64-bit words): [0] task counter, [1] skipped blocks,
-// [2..4] reduced result, [8..12] the single-matrix BatchMat, [16..] task results.
+// [2..4] reduced result, [5] deadline, [6] abort flag, [8..12] the
+// single-matrix BatchMat, [16..] task results.  Words 0..7 are cleared
+// before every launch.
+constexpr size_t kWsDeadline = 5;
+constexpr size_t kWsAbort = 6;
 constexpr size_t kWsBatchMat = 8;
 constexpr size_t kWsTaskOut = 16;
 
@@ -57,7 +65,7 @@ double now_ms();
 perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts, perm_plan_s &P,
                            void *storage = nullptr, size_t storage_bytes = 0);
 perm_status_t plan_device_setup(perm_plan_s &P);
-perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st);
+perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events = true);
 perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out);
 void describe(const perm_plan_s &P, perm_result_t *out);
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);

@@ -403,6 +403,9 @@ struct perm_server_s {
         ba.slot_bytes = slot_bytes;
         ba.nmat = (int)w->parts.size();
         ba.zero_skip = 1;
+        ba.timeout_ns = 0;
+        ba.deadline_word = nullptr;
+        ba.abort_flag = nullptr;
         int bps = 1;
         F.gf.occ(256, slot_bytes, &bps);
         const uint64_t grid_occ = (uint64_t)kSMCount * std::max(bps, 1);

@@ -229,3 +229,39 @@ def test_cfg2_full_permanent_against_stored_oracle_value():
     r = A.permanent(a)
     assert r.engine == A.PERM_ENGINE_CODEGEN
     assert rel_err(r.value, want) <= RTOL, (r.value, want)
+
+
+def test_repeated_compute_replays_a_graph_with_identical_results():
+    """From the second perm_compute on, a plan replays its launches as a CUDA
+    graph; results stay bit-identical, with and without the graph."""
+    for vals in ("f64", "01"):
+        a = synth.single_er(24, 0.25, 61, values=vals)
+        for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+            p = A.Plan(a, engine=engine)
+            rs = [p.compute() for _ in range(4)]
+            q = A.Plan(a, engine=engine, flags=A.PERM_FLAG_NO_GRAPH)
+            ns = [q.compute() for _ in range(2)]
+            for r in rs + ns:
+                assert (r.f64, r.f64_lo, r.i128_lo, r.i128_hi) == (rs[0].f64, rs[0].f64_lo, rs[0].i128_lo, rs[0].i128_hi)
+                assert r.ms_kernel > 0
+            p.close()
+            q.close()
+
+
+def test_device_deadline_stops_a_long_walk_and_the_context_survives():
+    """Failure detection without a fault: a 2^39-step walk with a 50 ms
+    device-side deadline stops taking work and reports TIMEOUT; the next
+    computes on the same context are correct."""
+    import time
+    big = synth.single_er(40, 0.1, 5, values="f64")
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        t0 = time.time()
+        with pytest.raises(A.PermError) as e:
+            A.permanent(big, engine=engine, timeout_ms=50)
+        assert e.value.status == A.PERM_ERR_TIMEOUT
+        assert time.time() - t0 < 30
+    small = synth.single_er(18, 0.3, 6, values="01")
+    assert A.permanent(small).value == oracle.ryser_gray(small)
+    res = A.batch([small, big], timeout_ms=50)
+    assert res[1].status == A.PERM_ERR_TIMEOUT
+    assert A.permanent(small, timeout_ms=60000).value == oracle.ryser_gray(small)
