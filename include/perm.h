@@ -302,6 +302,13 @@ perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opt
    the ALU roofline denominators of the FP64 and exact walks. */
 perm_status_t perm_issue_rates(void *stream, double *fp64_ops_per_s, double *imad_ops_per_s);
 
+/* The DFMA issue rate with every instruction guarded by a predicate that is
+   true (issued_on) or false (issued_off) in every lane: on GB300 the two are
+   equal, i.e. a false predicate does not free the FP64 pipe, which is why the
+   generic kernels dispatch to touched register slots instead of predicating
+   over all of them. */
+perm_status_t perm_fp64_predication_rates(void *stream, double *issued_on, double *issued_off);
+
 /* ------------------------------------------------------------- misc */
 
 const char *perm_status_string(perm_status_t s);

@@ -106,6 +106,7 @@ SIGNATURES = [
     ("perm_version", ctypes.c_char_p, []),
     ("perm_sizeof", c_i64, [c_i32]),
     ("perm_issue_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
+    ("perm_fp64_predication_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     ("perm_compute_noalloc", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), c_vp, ctypes.POINTER(Result)]),
     ("perm_checkpoint_run", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), ctypes.c_char_p, c_i32, c_i32, c_vp,
                                     ctypes.POINTER(Result)]),
@@ -315,6 +316,13 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fp64_predication_rates(stream: int = 0):
+    """(DFMA/s with a true predicate, DFMA/s with a false predicate)."""
+    a, b = c_dbl(), c_dbl()
+    check(lib().perm_fp64_predication_rates(c_vp(stream), ctypes.byref(a), ctypes.byref(b)), "predication rates")
+    return a.value, b.value
 
 
 def batch(mats, sequential: bool = False, stream: int = 0, **kw):
