@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -56,7 +57,13 @@ static int floor_log2(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
 // Builds the shared-memory image read by the generic kernels.
 // Image layout (see devmat.h): 16-byte header, column masks, group masks,
 // column offsets (u16), x0, then the values of columns 0..n-2 in slot order.
-static size_t devmat_head(int nmax) { return 16 + 16 * (size_t)nmax + 2 * (size_t)nmax; }
+static size_t devmat_head(int nmax) { return 32 + 11 * (size_t)nmax; }
+typedef pk::DevMat<16, double> DevMat16F;
+typedef pk::DevMat<32, int> DevMat32I;
+typedef pk::DevMat<48, double> DevMat48F;
+static_assert(offsetof(DevMat16F, x0) == 32 + 11 * 16, "image header");
+static_assert(offsetof(DevMat32I, x0) == 32 + 11 * 32, "image header");
+static_assert(offsetof(DevMat48F, x0) == 32 + 11 * 48, "image header");
 
 size_t devmat_bytes(int arith, int nmax, int nnz) {
     const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
@@ -90,11 +97,10 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
     hdr[2] = nnz;
     hdr[3] = (int32_t)bytes;
     uint64_t *colmask = reinterpret_cast<uint64_t *>(dst + 16);
-    uint64_t *grpmask = colmask + nmax;
-    uint16_t *colptr = reinterpret_cast<uint16_t *>(grpmask + nmax);
+    uint16_t *colptr = reinterpret_cast<uint16_t *>(colmask + nmax);
+    uint8_t *gbegin = reinterpret_cast<uint8_t *>(colptr + nmax);
     for (int p = 0; p + 1 < n; ++p) colmask[p] = L.colmask[p];
-    for (int g = 0; g < n; ++g)
-        for (int s = L.group_begin[g]; s < L.group_begin[g + 1]; ++s) grpmask[g] |= 1ull << s;
+    for (int g = 0; g <= n; ++g) gbegin[g] = (uint8_t)L.group_begin[g];
     unsigned char *x0 = dst + devmat_head(nmax);
     unsigned char *val = x0 + vsz * nmax;
     for (int s = 0; s < n; ++s) {

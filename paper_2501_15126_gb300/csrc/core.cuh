@@ -335,25 +335,35 @@ struct PairSteps {
     }
 };
 
-// Rolled form (policies with kRolled): the same 2^B steps as BlockSteps,
-// but as a loop with the column chosen at run time.  A data-driven policy
-// (the precompiled generic kernels) gains nothing from unrolling and loses
-// instruction-cache hits to it, so it takes this form; levels 1..B-1 of the
-// chain stay in registers (every Q index is a compile-time constant).
+// Rolled form (policies with kRolled): the same 2^B steps as the paired
+// form, as a loop over groups of four steps with the column of the first
+// step chosen at run time.  A data-driven policy (the precompiled generic
+// kernels) gains nothing from unrolling and loses instruction-cache hits to
+// it.  Steps 4t+1 and 4t+3 flip column 0 (signs + and -), step 4t+2 flips
+// column 1 with sign bit 2 of 4t+2, i.e. t's low bit; step 4t (t > 0) flips
+// column ctz(4t) >= 2.  The policy's pair_terms<S>() adds the terms of two
+// steps that differ by a column-0 flip and applies that flip.  Levels 1..B-1
+// of the chain stay in registers (every Q index is a compile-time constant).
 template <class Pol, class A, int Bv>
 __device__ __forceinline__ void rolled_block(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
                                              typename A::Blk &blk, int s_mid) {
+    static_assert(Bv >= 3, "the rolled block walks groups of four steps");
 #pragma unroll 1
-    for (int l = 1; l < (1 << Bv); ++l) {
-        const int j = __ffs(l) - 1;
-        const int s = (j == Bv - 1) ? s_mid : (((l >> (j + 1)) & 1) ? -1 : 1);
-        pol.flip_dyn(j, x, s);
+    for (int t = 0; t < (1 << (Bv - 2)); ++t) {
+        if (t != 0) {
+            const int l = t << 2;
+            const int j = __ffs(l) - 1;
+            const int s = (j == Bv - 1) ? s_mid : (((l >> (j + 1)) & 1) ? -1 : 1);
+            pol.flip_dyn(j, x, s);
 #pragma unroll
-        for (int M = Bv - 1; M >= 1; --M)
-            if (M <= j) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
-        const typename A::P p = pol.grp_dyn(0, x, Q[1]);
-        if (l & 1) A::template blk_add<-1>(blk, p);
-        else A::template blk_add<1>(blk, p);
+            for (int M = Bv - 1; M >= 2; --M)
+                if (M <= j) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
+            Q[1] = pol.grp_dyn(1, x, Q[2]);
+        }
+        pol.template pair_terms<1>(x, Q[1], blk);
+        pol.flip_dyn(1, x, (t & 1) ? -1 : 1);
+        Q[1] = pol.grp_dyn(1, x, Q[2]);
+        pol.template pair_terms<-1>(x, Q[1], blk);
     }
 }
 
@@ -402,7 +412,6 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
         if constexpr (Pol::kRolled) {
 #pragma unroll
             for (int M = Bv - 1; M >= 1; --M) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
-            A::template blk_add<1>(blk, pol.grp_dyn(0, x, Q[1]));
             rolled_block<Pol, A, Bv>(pol, x, Q, blk, s_mid);
         } else if constexpr (Pol::kPaired) {
             // steps 0 and 1 (column 0, sign +: bit 1 of 1 is 0), then pairs (2,3), (4,5), ...

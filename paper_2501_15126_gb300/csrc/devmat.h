@@ -57,7 +57,10 @@ struct BatchArgs {
 // image; only the first `bytes` bytes exist).  Slots are rows in the plan's
 // order; positions are columns in the plan's order.  Column p's values, in
 // slot order, are val[colptr[p] ..].  V is double (FP64 path) or int (exact
-// path: values doubled).
+// path: values doubled).  Slots are numbered group by group (a row's group is
+// the first column position that touches it), so group m is the contiguous
+// slot range [gbegin[m], gbegin[m+1]); group 0 is exactly column 0's rows.
+// For NMAX in {16, 32, 48} the header is 32 + 11 NMAX bytes, a multiple of 16.
 template <int NMAX, typename V>
 struct DevMat {
     int n;                              // dimension
@@ -65,8 +68,8 @@ struct DevMat {
     int nnz;                            // values stored (columns 0..n-2)
     int bytes;                          // size of this image, a multiple of 16
     unsigned long long colmask[NMAX];   // slots touched by column position p (p < n-1)
-    unsigned long long grpmask[NMAX];   // slots whose first touching column is m
     unsigned short colptr[NMAX];        // first value of column p
+    unsigned char gbegin[NMAX + 16];    // first slot of group m (m <= n; gbegin[n] = n)
     V x0[NMAX];                         // Nijenhuis-Wilf start values by slot
     V val[NMAX * NMAX];                 // nnz values, column after column
 };

@@ -30,18 +30,31 @@ namespace pk {
 
 // Register-slot access by a run-time index: a switch whose cases name x[k]
 // with a compile-time k, so x stays in registers.  The switch argument is
-// warp-uniform (a bit of a column or group mask), so it is a uniform jump,
-// and only the slots a column really touches cost an arithmetic instruction.
-// The compiler cannot prove the masks uniform; the walk's once-per-block
-// warp vote (core.cuh) is the reconvergence point that keeps the lanes
-// together.
+// warp-uniform (a bit of a column mask, a group boundary), so it is a uniform
+// jump, and only the slots a column really touches cost an arithmetic
+// instruction.  The compiler cannot prove the arguments uniform; the walk's
+// once-per-block warp vote (core.cuh) is the reconvergence point that keeps
+// the lanes together.
 // (A predicated loop over all NMAX slots would issue NMAX FP64 instructions
-// per flip whatever the mask: on GB300, where FP64 issues at 1/64 of FP32,
-// that dominates everything else.)
+// per flip whatever the mask: on GB300 a predicated-off DFMA costs the FP64
+// pipe as much as an executed one, and FP64 issues at 1/64 of FP32.)
+//
+// Contiguous slot ranges -- a row group, column 0's rows, the rows a column
+// touches first -- take one jump into a descending ladder of cases that fall
+// through to the end of the range, instead of one jump per slot.
 #define PERM_SLOT_CASES(F)                                                                              \
     F(0) F(1) F(2) F(3) F(4) F(5) F(6) F(7) F(8) F(9) F(10) F(11) F(12) F(13) F(14) F(15) F(16) F(17)   \
     F(18) F(19) F(20) F(21) F(22) F(23) F(24) F(25) F(26) F(27) F(28) F(29) F(30) F(31) F(32) F(33)     \
     F(34) F(35) F(36) F(37) F(38) F(39) F(40) F(41) F(42) F(43) F(44) F(45) F(46) F(47)
+#define PERM_SLOT_CASES_DOWN(F)                                                                         \
+    F(47) F(46) F(45) F(44) F(43) F(42) F(41) F(40) F(39) F(38) F(37) F(36) F(35) F(34) F(33) F(32)     \
+    F(31) F(30) F(29) F(28) F(27) F(26) F(25) F(24) F(23) F(22) F(21) F(20) F(19) F(18) F(17) F(16)    \
+    F(15) F(14) F(13) F(12) F(11) F(10) F(9) F(8) F(7) F(6) F(5) F(4) F(3) F(2) F(1) F(0)
+
+// Column masks: 32 bits are enough below 33 slots (one find-first-set per slot).
+template <int NMAX> struct SlotMask { typedef u64 T; static __device__ __forceinline__ int low(T v) { return ctz64(v); } };
+template <> struct SlotMask<16> { typedef u32 T; static __device__ __forceinline__ int low(T v) { return __ffs((int)v) - 1; } };
+template <> struct SlotMask<32> { typedef u32 T; static __device__ __forceinline__ int low(T v) { return __ffs((int)v) - 1; } };
 
 template <int NMAX, class A>
 struct GenericPol {
@@ -53,11 +66,18 @@ struct GenericPol {
     typedef typename A::P P;
     typedef typename A::V V;
     typedef DevMat<NMAX, V> M;
+    typedef typename SlotMask<NMAX>::T Mask;
 
     const M *m;
     P Qh[NMAX + 1];     // chain levels >= B (dynamic index: local memory)
 
     __device__ __forceinline__ explicit GenericPol(const M *mat) : m(mat) {}
+
+    __device__ __forceinline__ int gbegin(int g) const { return ((const volatile unsigned char *)m->gbegin)[g]; }
+    __device__ __forceinline__ Mask colmask(int j) const { return (Mask)((const volatile u64 *)m->colmask)[j]; }
+    __device__ __forceinline__ const volatile V *colvals(int j) const {
+        return m->val + ((const volatile unsigned short *)m->colptr)[j];
+    }
 
     // x[i] = x[i] + s * v for a run-time slot i
     __device__ __forceinline__ static void add_slot(X (&x)[NX], int i, V v, int s) {
@@ -71,63 +91,88 @@ struct GenericPol {
         default: break;
         }
     }
-    template <int S>
-    __device__ __forceinline__ static void add_slot_s(X (&x)[NX], int i, V v) {
-        switch (i) {
-#define PERM_ADDS_CASE(k)                                             \
-    case k:                                                           \
-        if constexpr (k < NMAX) x[k] = A::template upd<S>(x[k], v);   \
-        break;
-            PERM_SLOT_CASES(PERM_ADDS_CASE)
-#undef PERM_ADDS_CASE
+    // q * x[b] * ... * x[e-1] (b < e), highest slot first
+    __device__ __forceinline__ static P prod_range(const X (&x)[NX], int b, int e, P q) {
+        switch (e) {
+#define PERM_PROD_CASE(k)                                             \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            q = A::mul(q, x[k]);                                      \
+            if (k <= b) break;                                        \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_PROD_CASE)
+#undef PERM_PROD_CASE
         default: break;
-        }
-    }
-    __device__ __forceinline__ static X get_slot(const X (&x)[NX], int i) {
-        switch (i) {
-#define PERM_GET_CASE(k)                                              \
-    case k:                                                           \
-        if constexpr (k < NMAX) return x[k];                          \
-        break;
-            PERM_SLOT_CASES(PERM_GET_CASE)
-#undef PERM_GET_CASE
-        default: break;
-        }
-        return x[0];
-    }
-
-    template <int J, int S>
-    __device__ __forceinline__ void flip(X (&x)[NX]) {
-        u64 cm = ((const volatile u64 *)m->colmask)[J];
-        const volatile V *v = m->val + ((const volatile unsigned short *)m->colptr)[J];
-        while (cm) {
-            const int i = ctz64(cm);
-            cm &= cm - 1;
-            add_slot_s<S>(x, i, *v++);
-        }
-    }
-    template <int J>
-    __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
-    __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {
-        u64 cm = ((const volatile u64 *)m->colmask)[j];
-        const volatile V *v = m->val + ((const volatile unsigned short *)m->colptr)[j];
-        while (cm) {
-            const int i = ctz64(cm);
-            cm &= cm - 1;
-            add_slot(x, i, *v++, s);
-        }
-    }
-    __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
-        u64 gm = ((const volatile u64 *)m->grpmask)[g];
-        while (gm) {
-            const int i = ctz64(gm);
-            gm &= gm - 1;
-            q = A::mul(q, get_slot(x, i));
         }
         return q;
     }
+    // x[k] += s * w[k - b] for k in [b, e) (b < e), highest slot first
+    __device__ __forceinline__ static void add_range(X (&x)[NX], int b, int e, const volatile V *w, int s) {
+        switch (e) {
+#define PERM_ADDR_CASE(k)                                             \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            x[k] = A::upd_rt(x[k], w[k - b], s);                      \
+            if (k <= b) break;                                        \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_ADDR_CASE)
+#undef PERM_ADDR_CASE
+        default: break;
+        }
+    }
+
+    // Column j: the rows it shares with earlier groups one slot at a time,
+    // then its own group (the rows it touches first) as one range.
+    __device__ __forceinline__ void flip_dyn(int j, X (&x)[NX], int s) {
+        const int b = gbegin(j), e = gbegin(j + 1);
+        Mask cm = colmask(j) & (Mask)((1ull << b) - 1);
+        const volatile V *v = colvals(j);
+        while (cm) {
+            const int i = SlotMask<NMAX>::low(cm);
+            cm &= cm - 1;
+            add_slot(x, i, *v++, s);
+        }
+        if (b < e) add_range(x, b, e, v, s);
+    }
+    template <int J, int S>
+    __device__ __forceinline__ void flip(X (&x)[NX]) { flip_dyn(J, x, S); }
+    template <int J>
+    __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
+
+    __device__ __forceinline__ P grp_dyn(int g, const X (&x)[NX], P q) const {
+        const int b = gbegin(g), e = gbegin(g + 1);
+        return b < e ? prod_range(x, b, e, q) : q;
+    }
     template <int G>
     __device__ __forceinline__ P grp(const X (&x)[NX], P q) const { return grp_dyn(G, x, q); }
+
+    // Steps l (even) and l+1 of a block, l+1 flipping column 0 with sign S:
+    // both terms share Q_1 and differ only in column 0's rows, the slots
+    // [0, |R_0|), whose values are the first |R_0| of the image.  One ladder
+    // multiplies the rows before the flip, applies it, and multiplies after.
+    template <int S>
+    __device__ __forceinline__ void pair_terms(X (&x)[NX], P q1, typename A::Blk &blk) {
+        const volatile V *v = m->val;
+        P p0 = q1, p1 = q1;
+        switch (gbegin(1)) {
+#define PERM_PAIR_CASE(k)                                             \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            p0 = A::mul(p0, x[k]);                                    \
+            x[k] = A::template upd<S>(x[k], v[k]);                    \
+            p1 = A::mul(p1, x[k]);                                    \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_PAIR_CASE)
+#undef PERM_PAIR_CASE
+        default: break;
+        }
+        A::template blk_add<1>(blk, p0);
+        A::template blk_add<-1>(blk, p1);
+    }
+
     // x = x0 + sum of the columns set in Gray code G (columns < n-1 only)
     __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
 #pragma unroll
