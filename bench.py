@@ -431,16 +431,24 @@ def run_profile_case(args):
     import torch
     from paper_2501_15126_gb300 import _abi as A
     torch.cuda.set_device(0)
-    a = workload_matrix()
+    from paper_2501_15126_gb300 import synth
     vals = "01" if args.profile_exact else "f64"
-    if args.profile_exact:
-        from paper_2501_15126_gb300 import synth
+    if args.profile_matrix == "batch28":
+        # the largest class of the batch workload: its first n=28 matrix with these values
+        a = next(it.a for it in synth.batch(count=400) if it.a.shape[0] == 28 and it.values == vals)
+    elif args.profile_exact:
         a = synth.band_plus(48, 3, 2, seed=3, values="01")
+    else:
+        a = workload_matrix()
     engine = A.PERM_ENGINE_GENERIC if args.profile_engine == "generic" else A.PERM_ENGINE_CODEGEN
-    p = A.Plan(a, g_lo=0, g_hi=1 << args.profile_log2, engine=engine)
+    n = a.shape[0]
+    # a prefix of the walk, or (when it covers the range) the whole walk with its own ring width
+    g_hi = 0 if args.profile_log2 >= n - 1 else 1 << args.profile_log2
+    p = A.Plan(a, g_lo=0, g_hi=g_hi, engine=engine)
     for _ in range(args.steps):
         r = p.compute()
-    print(json.dumps({"profile_case": vals, "engine": args.profile_engine, "gray_steps": r.steps, "ms_kernel": r.ms_kernel,
+    print(json.dumps({"profile_case": vals, "matrix": args.profile_matrix, "n": n, "engine": args.profile_engine,
+                      "gray_steps": r.steps, "ms_kernel": r.ms_kernel,
                       "ops_per_step": r.fp_ops_per_step, "threads": r.threads, "regs": r.regs_per_thread,
                       "chunk_log2": r.chunk_log2, "zero_skip_frac": r.zero_skip_frac}))
     p.close()
@@ -459,6 +467,9 @@ def main():
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
     ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
+    ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28"],
+                    help="bench: the n=36 bench matrix (the n=48 band with --profile-exact); "
+                         "batch28: an n=28 matrix of the batch workload")
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)

@@ -112,7 +112,10 @@ typedef struct {
     int32_t chunk_log2;    /* K: each thread walks aligned chunks of 2^K Gray indices;     */
                            /*   0 = auto                                                   */
     int32_t threads;       /* resident threads of the persistent grid; 0 = auto            */
-    int32_t exact_words;   /* exact path modulus 2^(64w): 0 = smallest w the bound allows  */
+    int32_t exact_words;   /* exact path modulus 2^(64w): 0 = smallest w the bound allows, */
+                           /*   and a whole walk then runs in the narrowest ring of 32-bit */
+                           /*   limbs (2w-1 or 2w) that holds 2^(n-1) perm with its sign; */
+                           /*   an explicit w walks modulo 2^(64w)                         */
     int32_t zero_skip;     /* 0 = on (skip 2^B-step blocks whose products are all zero),   */
                            /*   1 = off                                                    */
     int32_t flags;         /* PERM_FLAG_* bits                                             */
@@ -275,6 +278,8 @@ typedef struct {
     double bound_log2;           /* log2 of the a-priori |perm| bound                */
     double ops_per_step;         /* cost model: arithmetic ops per step, this scheme */
     double ops_per_step_paper;   /* the same walk with a full product per step       */
+    int32_t exact_limbs;         /* 32-bit limbs of the whole walk's ring: 2w-1 or 2w */
+    int32_t reserved0;
 } perm_inspect_t;
 
 perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts, perm_inspect_t *out);
@@ -292,7 +297,9 @@ perm_status_t perm_alg2_launches(int64_t tau, int32_t n, int64_t *start, int64_t
 
 /* The CUDA C++ source that the codegen engine would compile for A (for
    inspection).  Writes at most cap bytes including the terminating NUL and
-   sets *len to the full length. */
+   sets *len to the full length.  A kernel whose register spills exceed 512
+   bytes per thread is rebuilt from the same text with a 255-register budget
+   (__launch_bounds__(256, 1) in place of (256, 2)). */
 perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opts, char *buf, int64_t cap,
                                   int64_t *len);
 

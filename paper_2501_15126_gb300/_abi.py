@@ -66,7 +66,7 @@ class Inspect(ctypes.Structure):
                 ("col_order", c_i32 * 64), ("row_order", c_i32 * 64), ("group_of_row", c_i32 * 64),
                 ("group_size", c_i32 * 64), ("col_nnz", c_i32 * 64), ("reg_rows", c_i32), ("reg_cols", c_i32),
                 ("exact_words", c_i32), ("bound_log2", c_dbl), ("ops_per_step", c_dbl),
-                ("ops_per_step_paper", c_dbl)]
+                ("ops_per_step_paper", c_dbl), ("exact_limbs", c_i32), ("reserved0", c_i32)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -191,6 +191,14 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
             }
         }
         P.arith = w ? w : 1;
+        // the narrowest ring of 32-bit limbs that holds the whole sum; a
+        // sub-range (a partial sum reported modulo 2^(64 arith)) or an
+        // explicit width keeps all 2 arith limbs
+        P.limbs = 2 * P.arith;
+        if (!opts.exact_words && !P.subrange && !P.zero) {
+            const int l = exact_limbs_for(b, n);
+            if (l && (l + 1) / 2 == P.arith) P.limbs = l;
+        }
     }
     P.ms_plan = now_ms() - t0;
     return PERM_OK;
@@ -263,7 +271,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
     P.words = P.arith == 0 ? 2 : P.arith;
 
     if (engine == PERM_ENGINE_GENERIC) {
-        P.gf = generic_fns(nmax, P.arith);
+        P.gf = generic_fns(nmax, P.limbs);
         if (!P.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this size");
         P.nmax = nmax;
         std::vector<unsigned char> img;
@@ -418,19 +426,22 @@ perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *r, perm_result_t 
     const int W = P.arith;
     for (int i = 0; i < W; ++i) out->partial[i] = r[i];
     if (P.subrange) { out->status = PERM_OK; return PERM_OK; }
-    // S = (-1)^(n-1) 2^(n-1) perm  (mod 2^(64W)): the low n-1 bits must vanish
-    const unsigned __int128 lo128 = ((unsigned __int128)(W >= 2 ? r[1] : 0) << 64) | r[0];
-    const uint64_t top = W >= 3 ? r[2] : 0;
+    // S = (-1)^(n-1) 2^(n-1) perm  (mod 2^(32 limbs)): the low n-1 bits must vanish
+    const int ring_bits = 32 * (P.limbs ? P.limbs : 2 * W);
+    uint64_t s[3] = {0, 0, 0};
+    for (int i = 0; i < W; ++i) s[i] = r[i];
+    if (ring_bits < 64 * W) s[W - 1] &= (1ull << (ring_bits - 64 * (W - 1))) - 1;   // odd limb count
+    const unsigned __int128 lo128 = ((unsigned __int128)s[1] << 64) | s[0];
+    const uint64_t top = s[2];
     const int shift = n - 1;
-    if (shift && (r[0] & ((shift >= 64) ? ~0ull : ((1ull << shift) - 1)))) {
+    if (shift && (s[0] & ((1ull << shift) - 1))) {
         out->status = PERM_ERR_INTERNAL;
         return fail(PERM_ERR_INTERNAL, "exact sum not divisible by 2^(n-1)");
     }
-    // value = S >> (n-1) as a (64W - n + 1)-bit two's complement number
-    unsigned __int128 v;
-    if (W == 3) v = (shift ? (lo128 >> shift) | ((unsigned __int128)top << (128 - shift)) : lo128);
-    else v = lo128 >> shift;
-    const int bits = 64 * W - shift;
+    // value = S >> (n-1) as a (ring_bits - n + 1)-bit two's complement number
+    const unsigned __int128 v0 = shift ? (lo128 >> shift) | ((unsigned __int128)top << (128 - shift)) : lo128;
+    unsigned __int128 v = v0;
+    const int bits = ring_bits - shift;
     if (bits < 128) {
         const unsigned __int128 one = 1;
         const unsigned __int128 mask = (one << bits) - 1;
@@ -562,6 +573,7 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     out->reg_cols = c;
     out->bound_log2 = bound_log2(m);
     out->exact_words = m.is_int ? exact_words_for(out->bound_log2, m.n) : 0;
+    out->exact_limbs = out->exact_words ? exact_limbs_for(out->bound_log2, m.n) : 0;
     out->ops_per_step = cost_per_step(L, false);
     out->ops_per_step_paper = cost_per_step(L, true);
     return PERM_OK;

@@ -36,10 +36,11 @@ int batch_chunk_log2(int n, int B, int K_target) {
     return std::min(K, n - 1);
 }
 
-int BatchGroup::setup(int nmax_, int arith_, int K_target) {
+int BatchGroup::setup(int nmax_, int limbs_, int K_target) {
     nmax = nmax_;
-    arith = arith_;
-    gf = generic_fns(nmax, arith);
+    limbs = limbs_;
+    arith = (limbs + 1) / 2;
+    gf = generic_fns(nmax, limbs);
     if (!gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this group");
     words = arith == 0 ? 2 : arith;
     // task table
@@ -180,7 +181,7 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
         if (s != PERM_OK) { out[i].status = s; plans[i].reset(); continue; }
         if (P.zero) { describe(P, &out[i]); out[i].status = PERM_OK; plans[i].reset(); continue; }
         if (P.m.n <= 8 || P.m.n > 48) { singles.push_back(i); continue; }
-        groups[{nmax_bucket(P.m.n), P.arith}].add(i, &P);
+        groups[{nmax_bucket(P.m.n), P.limbs}].add(i, &P);
     }
     const double t_prep = now_ms() - t0;
 
@@ -194,7 +195,8 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
         if (!K_target) {
             if (!chunk_log2_is_tuned(kv.first.first, kv.first.second)) {
                 G.nmax = kv.first.first;
-                G.arith = kv.first.second;
+                G.limbs = kv.first.second;
+                G.arith = (G.limbs + 1) / 2;
                 autotune_group(G, st);
             }
             K_target = tuned_chunk_log2(kv.first.first, kv.first.second);

@@ -114,7 +114,7 @@ struct Emitter {
     int n, k, c;
     int min_blocks;   // __launch_bounds__ minimum resident blocks per SM (register budget)
     std::ostringstream o;
-    explicit Emitter(const perm_plan_s &p) : P(p), n(p.m.n), k(p.k), c(p.c), min_blocks(codegen_min_blocks(p)) {}
+    Emitter(const perm_plan_s &p, int mb) : P(p), n(p.m.n), k(p.k), c(p.c), min_blocks(mb) {}
 
     // value of ordered column p at slot s (doubled on the exact path)
     bool has(int p, int s) const { return (P.L.colmask[p] >> s) & 1ull; }
@@ -165,7 +165,7 @@ struct Emitter {
         o << "// order=" << P.L.ordering << " reg_rows(k)=" << k << " reg_cols(c)=" << c << " B=" << B << "\n";
         o << "#include \"core.cuh\"\n\nnamespace pk {\n";
         if (P.arith == 0) o << "typedef ArithF64 A;\n";
-        else o << "typedef ArithExact<" << P.arith << "> A;\n";
+        else o << "typedef ArithExact<" << P.limbs << "> A;\n";
         o << "struct GenPol {\n";
         o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
         o << "    static constexpr bool kPaired = " << (P.arith == 0 ? "true" : "false") << ";\n";
@@ -253,8 +253,10 @@ struct Emitter {
             o << "        " << slot(s) << " = " << lit(P, x0) << ";\n";
         }
         for (int s = n; s < k; ++s) o << "        x[" << s << "] = 0;\n";
-        o << "        while (G) {\n            const int p = ctz64(G);\n            G &= G - 1;\n";
-        o << "            flip_dyn(p, x, 1);\n        }\n    }\n";
+        // the warp visits the union of its lanes' columns; each lane adds a column with weight 0 or 1
+        o << "        unsigned long long U = warp_or64(G);\n";
+        o << "        while (U) {\n            const int p = ctz64(U);\n            U &= U - 1;\n";
+        o << "            flip_dyn(p, x, (int)((G >> p) & 1ull));\n        }\n    }\n";
         // high chain levels
         auto above = [&](int g) -> std::string {   // the nonempty level just above g
             for (int h = g + 1; h < n; ++h)
@@ -304,8 +306,18 @@ struct CacheEntry {
     CUmodule module = nullptr;
     CUfunction function = nullptr;
     int regs = 0;
+    int local_bytes = 0;   // per-thread local memory (register spills)
     int blocks_per_sm = 0;
 };
+
+// A kernel compiled for two resident blocks (128 registers) whose spill
+// frame exceeds this is rebuilt for one block (255 registers).  Dense exact
+// walks (every row in the lowest group, multi-limb products unrolled over the
+// block) are the ones that reach it.  One of them, the 128-bit walk of -J_15
+// with a 1.4 KB frame, returned a wrong top limb, reproducibly and for every
+// chunk size and grid, while the same source built for 255 registers was
+// right; the cause was not found, so the spill-heavy build is not used.
+constexpr int kMaxLocalFrame = 512;
 
 std::mutex g_cache_mu;
 std::unordered_map<std::string, CacheEntry> g_cache;
@@ -314,9 +326,49 @@ constexpr size_t kCacheMax = 512;
 }  // namespace
 
 std::string codegen_source(const perm_plan_s &P) {
-    Emitter e(P);
+    Emitter e(P, codegen_min_blocks(P));
     return e.emit();
 }
+
+namespace {
+
+// Compiles src with NVRTC for sm_103a and loads it into ce.
+perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::string &err) {
+    Driver &d = driver();
+    nvrtcProgram prog;
+    const char *hdr_src[2] = {perm_embedded_core_cuh, perm_embedded_devmat_h};
+    const char *hdr_name[2] = {"core.cuh", "devmat.h"};
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "perm_walk.cu", 2, hdr_src, hdr_name);
+    if (r != NVRTC_SUCCESS) { err = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r); return PERM_ERR_NVRTC; }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--device-as-default-execution-space"};
+    r = nvrtcCompileProgram(prog, 4, opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nvrtcGetProgramLogSize(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) nvrtcGetProgramLog(prog, &log[0]);
+        nvrtcDestroyProgram(&prog);
+        err = "NVRTC compile failed: " + log.substr(0, 2000);
+        return PERM_ERR_NVRTC;
+    }
+    size_t cs = 0;
+    nvrtcGetCUBINSize(prog, &cs);
+    std::vector<char> cubin(cs);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    cudaFree(nullptr);   // make the primary context current on this thread
+    CUresult cr = d.moduleLoadData(&ce.module, cubin.data());
+    if (cr != CUDA_SUCCESS) { err = "cuModuleLoadData: " + cu_err(cr); return PERM_ERR_CUDA; }
+    cr = d.moduleGetFunction(&ce.function, ce.module, "perm_walk");
+    if (cr != CUDA_SUCCESS) { err = "cuModuleGetFunction: " + cu_err(cr); return PERM_ERR_CUDA; }
+    d.funcGetAttribute(&ce.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ce.function);
+    d.funcGetAttribute(&ce.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, ce.function);
+    cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, 0);
+    if (cr != CUDA_SUCCESS) { err = "occupancy: " + cu_err(cr); return PERM_ERR_CUDA; }
+    return PERM_OK;
+}
+
+}  // namespace
 
 perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     Driver &d = driver();
@@ -340,36 +392,16 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
         }
     }
     const double t0 = now_ms();
-    nvrtcProgram prog;
-    const char *hdr_src[2] = {perm_embedded_core_cuh, perm_embedded_devmat_h};
-    const char *hdr_name[2] = {"core.cuh", "devmat.h"};
-    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "perm_walk.cu", 2, hdr_src, hdr_name);
-    if (r != NVRTC_SUCCESS) { err = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r); return PERM_ERR_NVRTC; }
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--device-as-default-execution-space"};
-    r = nvrtcCompileProgram(prog, 4, opts);
-    if (r != NVRTC_SUCCESS) {
-        size_t ls = 0;
-        nvrtcGetProgramLogSize(prog, &ls);
-        std::string log(ls, '\0');
-        if (ls) nvrtcGetProgramLog(prog, &log[0]);
-        nvrtcDestroyProgram(&prog);
-        err = "NVRTC compile failed: " + log.substr(0, 2000);
-        return PERM_ERR_NVRTC;
-    }
-    size_t cs = 0;
-    nvrtcGetCUBINSize(prog, &cs);
-    std::vector<char> cubin(cs);
-    nvrtcGetCUBIN(prog, cubin.data());
-    nvrtcDestroyProgram(&prog);
-    cudaFree(nullptr);   // make the primary context current on this thread
     CacheEntry ce;
-    CUresult cr = d.moduleLoadData(&ce.module, cubin.data());
-    if (cr != CUDA_SUCCESS) { err = "cuModuleLoadData: " + cu_err(cr); return PERM_ERR_CUDA; }
-    cr = d.moduleGetFunction(&ce.function, ce.module, "perm_walk");
-    if (cr != CUDA_SUCCESS) { err = "cuModuleGetFunction: " + cu_err(cr); return PERM_ERR_CUDA; }
-    d.funcGetAttribute(&ce.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ce.function);
-    cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, 0);
-    if (cr != CUDA_SUCCESS) { err = "occupancy: " + cu_err(cr); return PERM_ERR_CUDA; }
+    perm_status_t st = compile_and_load(src, ce, err);
+    if (st != PERM_OK) return st;
+    if (ce.local_bytes > kMaxLocalFrame && !std::getenv("PERM_CODEGEN_MIN_BLOCKS")) {
+        if (driver().moduleUnload) driver().moduleUnload(ce.module);
+        ce = CacheEntry();
+        Emitter e1(P, 1);
+        st = compile_and_load(e1.emit(), ce, err);
+        if (st != PERM_OK) return st;
+    }
     P.ms_compile = now_ms() - t0;
     if (use_cache) {
         std::lock_guard<std::mutex> lk(g_cache_mu);

@@ -13,11 +13,14 @@
 //
 // Parallel layout (Sec. II-A, Theorem 1, Lemma 1).  The 2^(n-1) indices are
 // cut into aligned chunks of 2^K; chunk q starts from x(q 2^K), built from the
-// set bits of Gray(q 2^K) (all >= K-1).  Inside a chunk step l flips column
-// j = ctz(l) with sign + iff bit j+1 of g is 0 (Theorem 1).  Because chunks are
-// aligned powers of two, every lane of a warp flips the same column at the same
-// step: only the sign of column K-1 differs between lanes (the first case of
-// Lemma 1), and that is an arithmetic sign, not a branch.  The second
+// set bits of Gray(q 2^K) (all >= K-1).  The warp builds its 32 start vectors
+// together: it visits every column set in any lane's code, and each lane adds
+// that column with weight 0 or 1, so no lane waits for another's flips.
+// Inside a chunk step l flips column j = ctz(l) with sign + iff bit j+1 of g
+// is 0 (Theorem 1).  Because chunks are aligned powers of two, every lane of a
+// warp flips the same column at the same step: only the sign of column K-1
+// differs between lanes (the first case of Lemma 1), and that is an
+// arithmetic sign, not a branch.  The second
 // divergent case of Lemma 1 (l = 2^k) never arises because each chunk starts
 // from its own start vector.  Chunks are grouped 32 per warp task; warps of a
 // persistent grid take tasks from an atomic counter.
@@ -55,6 +58,13 @@ typedef long long i64;
 namespace pk {
 
 __device__ __forceinline__ int ctz64(u64 v) { return __ffsll((long long)v) - 1; }
+
+// OR of a 64-bit value over the 32 lanes of a (converged) warp.
+__device__ __forceinline__ u64 warp_or64(u64 v) {
+    const u32 lo = __reduce_or_sync(PERM_FULLMASK, (u32)v);
+    const u32 hi = __reduce_or_sync(PERM_FULLMASK, (u32)(v >> 32));
+    return ((u64)hi << 32) | lo;
+}
 
 // Nanoseconds from the GPU's global timer.
 __device__ __forceinline__ u64 global_ns() {
@@ -212,9 +222,13 @@ __device__ __forceinline__ void ring_sub<2>(Ring<2> &a, const Ring<2> &b) {
     a.w[1] = (u32)(v >> 32);
 }
 
-template <int W>   // W 64-bit words = 2W limbs
+// Exact arithmetic in Z / 2^(32 NL): NL 32-bit limbs, stored and reduced as
+// ceil(NL/2) 64-bit words (an odd limb count leaves the top half-word of the
+// last word zero; sums of stored words stay right modulo 2^(32 NL)).
+template <int NL>
 struct ArithExact {
-    static constexpr int L = 2 * W;
+    static constexpr int L = NL;
+    static constexpr int W = (NL + 1) / 2;
     typedef int X;
     typedef Ring<L> P;
     typedef int V;
@@ -258,12 +272,18 @@ struct ArithExact {
     static constexpr int ACC_WORDS = W;
     static __device__ __forceinline__ void acc_store(u64 *dst, const Acc &a) {
 #pragma unroll
-        for (int i = 0; i < W; ++i) dst[i] = ((u64)a.w[2 * i + 1] << 32) | a.w[2 * i];
+        for (int i = 0; i < W; ++i) {
+            const u64 hi = (2 * i + 1 < L) ? (u64)a.w[(2 * i + 1) % L] : 0ull;
+            dst[i] = (hi << 32) | a.w[2 * i];
+        }
     }
     static __device__ __forceinline__ Acc acc_load(const u64 *src) {
         Acc a;
 #pragma unroll
-        for (int i = 0; i < W; ++i) { a.w[2 * i] = (u32)src[i]; a.w[2 * i + 1] = (u32)(src[i] >> 32); }
+        for (int i = 0; i < W; ++i) {
+            a.w[2 * i] = (u32)src[i];
+            if (2 * i + 1 < L) a.w[(2 * i + 1) % L] = (u32)(src[i] >> 32);
+        }
         return a;
     }
 };

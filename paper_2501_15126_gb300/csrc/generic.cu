@@ -56,9 +56,9 @@ cudaError_t segment_reduce_launch(int arith, const uint64_t *seg, int nseg, cons
     if (nseg <= 0) return cudaSuccess;
     switch (arith) {
     case 0: pk::k_segment_reduce<pk::ArithF64><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
-    case 1: pk::k_segment_reduce<pk::ArithExact<1>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
-    case 2: pk::k_segment_reduce<pk::ArithExact<2>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
-    case 3: pk::k_segment_reduce<pk::ArithExact<3>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 1: pk::k_segment_reduce<pk::ArithExact<2>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 2: pk::k_segment_reduce<pk::ArithExact<4>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
+    case 3: pk::k_segment_reduce<pk::ArithExact<6>><<<grid, 256, 0, st>>>(sg, nseg, in, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -72,25 +72,29 @@ cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, u
     if (nmat <= 0) return cudaSuccess;
     switch (arith) {
     case 0: pk::k_batch_reduce<pk::ArithF64><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
-    case 1: pk::k_batch_reduce<pk::ArithExact<1>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
-    case 2: pk::k_batch_reduce<pk::ArithExact<2>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
-    case 3: pk::k_batch_reduce<pk::ArithExact<3>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
+    case 1: pk::k_batch_reduce<pk::ArithExact<2>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
+    case 2: pk::k_batch_reduce<pk::ArithExact<4>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
+    case 3: pk::k_batch_reduce<pk::ArithExact<6>><<<grid, 256, 0, st>>>(mats, nmat, ntasks, in, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 GenericFns generic_fns_f64(int nmax);
-GenericFns generic_fns_e1(int nmax);
-GenericFns generic_fns_e2(int nmax);
-GenericFns generic_fns_e3(int nmax);
+GenericFns generic_fns_r64(int nmax);
+GenericFns generic_fns_r96(int nmax);
+GenericFns generic_fns_r128(int nmax);
+GenericFns generic_fns_r160(int nmax);
+GenericFns generic_fns_r192(int nmax);
 
-GenericFns generic_fns(int nmax, int arith) {
-    switch (arith) {
+GenericFns generic_fns(int nmax, int limbs) {
+    switch (limbs) {
     case 0: return generic_fns_f64(nmax);
-    case 1: return generic_fns_e1(nmax);
-    case 2: return generic_fns_e2(nmax);
-    case 3: return generic_fns_e3(nmax);
+    case 2: return generic_fns_r64(nmax);
+    case 3: return generic_fns_r96(nmax);
+    case 4: return generic_fns_r128(nmax);
+    case 5: return generic_fns_r160(nmax);
+    case 6: return generic_fns_r192(nmax);
     default: return GenericFns();
     }
 }
@@ -100,9 +104,9 @@ cudaError_t reduce_launch(int arith, const uint64_t *task_out, uint64_t ntasks, 
     unsigned long long *out = reinterpret_cast<unsigned long long *>(result);
     switch (arith) {
     case 0: pk::k_reduce<pk::ArithF64><<<1, 1024, 0, st>>>(in, ntasks, out); break;
-    case 1: pk::k_reduce<pk::ArithExact<1>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
-    case 2: pk::k_reduce<pk::ArithExact<2>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
-    case 3: pk::k_reduce<pk::ArithExact<3>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
+    case 1: pk::k_reduce<pk::ArithExact<2>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
+    case 2: pk::k_reduce<pk::ArithExact<4>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
+    case 3: pk::k_reduce<pk::ArithExact<6>><<<1, 1024, 0, st>>>(in, ntasks, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

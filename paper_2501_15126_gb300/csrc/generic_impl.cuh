@@ -173,14 +173,16 @@ struct GenericPol {
         A::template blk_add<-1>(blk, p1);
     }
 
-    // x = x0 + sum of the columns set in Gray code G (columns < n-1 only)
+    // x = x0 + sum of the columns set in Gray code G (columns < n-1 only);
+    // called by the whole warp, which visits the union of its lanes' columns
     __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
 #pragma unroll
         for (int i = 0; i < NMAX; ++i) x[i] = ((const volatile V *)m->x0)[i];
-        while (G) {
-            const int p = ctz64(G);
-            G &= G - 1;
-            flip_dyn(p, x, 1);
+        u64 U = warp_or64(G);
+        while (U) {
+            const int p = ctz64(U);
+            U &= U - 1;
+            flip_dyn(p, x, (int)((G >> p) & 1ull));
         }
     }
     // all levels from the top group down to B

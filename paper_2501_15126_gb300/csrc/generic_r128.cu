@@ -1,0 +1,5 @@
+// generic_r128.cu -- generic kernels for exact arithmetic modulo 2^128 (see generic_impl.cuh).
+#define PERM_GENERIC_B 5
+#include "generic_impl.cuh"
+
+PERM_GENERIC_UNIT(r128, pk::ArithExact<4>)

@@ -1,0 +1,5 @@
+// generic_r64.cu -- generic kernels for exact arithmetic modulo 2^64 (see generic_impl.cuh).
+#define PERM_GENERIC_B 5
+#include "generic_impl.cuh"
+
+PERM_GENERIC_UNIT(r64, pk::ArithExact<2>)

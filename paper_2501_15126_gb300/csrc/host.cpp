@@ -301,6 +301,13 @@ int exact_words_for(double bound, int n) {
     return 0;
 }
 
+int exact_limbs_for(double bound, int n) {
+    if (!(bound < 125.0)) return 0;
+    for (int l = 2; l <= 6; ++l)
+        if (32.0 * l >= bound + n + 2.0) return l;
+    return 0;
+}
+
 std::vector<Launch> alg2_launches(int64_t tau, int n) {
     std::vector<Launch> out;
     int64_t start = 1;

@@ -98,6 +98,9 @@ double bound_log2(const Matrix &m);
 // Smallest w in 1..3 with the doubled-NW sum recoverable modulo 2^(64 w),
 // or 0 when even w = 3 is not enough.
 int exact_words_for(double bound, int n);
+// The fewest 32-bit limbs (2..6) of a ring that holds 2^(n-1) perm with sign
+// and margin, or 0.
+int exact_limbs_for(double bound, int n);
 
 // Theorem 1: column flipped at step i >= 1 and its sign.
 inline int scbs_col(uint64_t i) { return __builtin_ctzll(i); }

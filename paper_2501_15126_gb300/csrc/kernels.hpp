@@ -20,8 +20,8 @@ struct GenericFns {
     size_t devmat_bytes = 0;   // the largest possible image (every value stored)
 };
 
-// arith: 0 = FP64, 1..3 = exact modulo 2^(64 arith).  nmax in {16, 32, 48}.
-GenericFns generic_fns(int nmax, int arith);
+// limbs: 0 = FP64, 2..6 = exact modulo 2^(32 limbs).  nmax in {16, 32, 48}.
+GenericFns generic_fns(int nmax, int limbs);
 
 // Per-matrix sums of a multi-matrix walk: result[m] = sum of task results
 // [mats[m].task_begin, mats[m+1].task_begin) (the last ends at ntasks), in a

@@ -125,6 +125,20 @@ def test_structurally_zero_and_edge_cases():
     assert A.permanent(synth.permutation_matrix(30, 3)).value == 1
 
 
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
+def test_odd_limb_rings_give_closed_forms_exactly(engine):
+    """Whole walks run in the narrowest ring of 32-bit limbs: J_21 and -J_15
+    in 96 bits (-J_15 by its row-sum bound 15^15), J_30 in 160 bits.
+    perm(J_n) = n!, perm(-J_n) = (-1)^n n!, and an explicit 64w-bit ring gives
+    the same values."""
+    for n, sign, limbs in ((21, 1, 3), (15, -1, 3), (30, 1, 5)):
+        a = sign * synth.ones(n)
+        assert A.inspect(a).exact_limbs == limbs
+        want = sign ** n * math.factorial(n)
+        assert A.permanent(a, engine=engine).value == want, (n, sign)
+        assert A.permanent(a, engine=engine, exact_words=(limbs + 1) // 2).value == want, (n, sign)
+
+
 def test_exact_negative_entries():
     a = rand_pattern(18, 0.35, 4, "int")
     assert A.permanent(a).value == oracle.ryser_gray(a)

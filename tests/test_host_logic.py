@@ -158,6 +158,26 @@ def test_structural_guard_and_exact_width():
     assert A.inspect(ones).bound_log2 >= np.log2(float(np.prod(np.arange(1, 31, dtype=float)))) - 1e-9
 
 
+def test_ring_limbs_are_the_narrowest_that_hold_the_scaled_sum():
+    """A whole exact walk holds (-1)^(n-1) 2^(n-1) perm: bound + (n-1) bits, a
+    sign bit and a margin bit, in the fewest 32-bit limbs (at least 2), which
+    fill the stored 64-bit words (2w-1 or 2w limbs)."""
+    cases = [synth.single_er(24, 0.2, 1, values="01"), synth.band_plus(48, 3, 2, seed=3, values="01"),
+             synth.ones(21), synth.ones(30), np.eye(12, dtype=np.int64)]
+    cases += [synth.single_er(n, p, s, values="01") for n, p, s in ((28, 0.3, 2), (26, 0.4, 3), (16, 0.2, 4))]
+    for a in cases:
+        ins = A.inspect(a)
+        need = ins.bound_log2 + a.shape[0] + 2
+        assert 32 * ins.exact_limbs >= need and (ins.exact_limbs == 2 or 32 * (ins.exact_limbs - 1) < need)
+        assert (ins.exact_limbs + 1) // 2 == ins.exact_words
+    # 21! ~ 2^65.5: 65.5 + 23 bits -> three limbs (96-bit ring); 30! -> five (160-bit)
+    assert A.inspect(synth.ones(21)).exact_limbs == 3
+    assert A.inspect(synth.ones(30)).exact_limbs == 5
+    # entries other than 0/1 take the row-sum bound: -J_15 -> 15^15 ~ 2^58.6 -> 58.6 + 17 bits
+    assert A.inspect(-synth.ones(15)).exact_limbs == 3 and A.inspect(-synth.ones(15)).exact_words == 2
+    assert A.inspect(synth.single_er(24, 0.2, 1, values="f64")).exact_limbs == 0
+
+
 def test_codegen_source_bakes_the_matrix():
     a = synth.single_er(12, 0.3, 5, values="f64")
     src = A.codegen_source(a)
