@@ -57,13 +57,13 @@ static int floor_log2(uint64_t v) { return v ? 63 - __builtin_clzll(v) : -1; }
 // Builds the shared-memory image read by the generic kernels.
 // Image layout (see devmat.h): 16-byte header, column masks, group masks,
 // column offsets (u16), x0, then the values of columns 0..n-2 in slot order.
-static size_t devmat_head(int nmax) { return 32 + 11 * (size_t)nmax; }
+static size_t devmat_head(int nmax) { return 48 + 12 * (size_t)nmax; }
 typedef pk::DevMat<16, double> DevMat16F;
 typedef pk::DevMat<32, int> DevMat32I;
 typedef pk::DevMat<48, double> DevMat48F;
-static_assert(offsetof(DevMat16F, x0) == 32 + 11 * 16, "image header");
-static_assert(offsetof(DevMat32I, x0) == 32 + 11 * 32, "image header");
-static_assert(offsetof(DevMat48F, x0) == 32 + 11 * 48, "image header");
+static_assert(offsetof(DevMat16F, x0) == 48 + 12 * 16, "image header");
+static_assert(offsetof(DevMat32I, x0) == 48 + 12 * 32, "image header");
+static_assert(offsetof(DevMat48F, x0) == 48 + 12 * 48, "image header");
 
 size_t devmat_bytes(int arith, int nmax, int nnz) {
     const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
@@ -93,14 +93,16 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
     std::memset(dst, 0, bytes);
     int32_t *hdr = reinterpret_cast<int32_t *>(dst);
     hdr[0] = n;
-    hdr[1] = L.top;
+    hdr[1] = L.top_dual;
     hdr[2] = nnz;
     hdr[3] = (int32_t)bytes;
     uint64_t *colmask = reinterpret_cast<uint64_t *>(dst + 16);
     uint16_t *colptr = reinterpret_cast<uint16_t *>(colmask + nmax);
     uint8_t *gbegin = reinterpret_cast<uint8_t *>(colptr + nmax);
+    uint8_t *sbegin = gbegin + nmax + 16;
     for (int p = 0; p + 1 < n; ++p) colmask[p] = L.colmask[p];
     for (int g = 0; g <= n; ++g) gbegin[g] = (uint8_t)L.group_begin[g];
+    for (int g = 0; g <= n; ++g) sbegin[g] = (uint8_t)L.s_begin[g];
     unsigned char *x0 = dst + devmat_head(nmax);
     unsigned char *val = x0 + vsz * nmax;
     for (int s = 0; s < n; ++s) {
@@ -401,7 +403,9 @@ void describe(const perm_plan_s &P, perm_result_t *out) {
     out->steps = P.zero ? 0 : P.g_hi - P.g_lo;
     out->ms_plan = P.ms_plan;
     out->ms_compile = P.ms_compile;
-    out->fp_ops_per_step = P.ops_per_step;
+    out->fp_ops_per_step = (P.engine == PERM_ENGINE_GENERIC && !P.direct && P.arith == 0 && P.m.n <= 32)
+                               ? cost_per_step_dual(P.L, true)
+                               : P.ops_per_step;
     out->exact_words = P.m.is_int ? P.arith : 0;
 }
 

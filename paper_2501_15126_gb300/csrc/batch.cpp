@@ -14,6 +14,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -170,15 +172,36 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double t0 = now_ms();
 
+    // host preprocessing (validation, matching check, ordering, exact width)
+    // of every matrix, spread over host threads: plans are independent
     std::vector<std::unique_ptr<perm_plan_s>> plans(count);
+    std::vector<perm_status_t> prep(count, PERM_OK);
+    {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nthreads = count >= 256 ? (int)std::min(hw, 16u) : 1;
+        auto work = [&](int t) {
+            for (int32_t i = t; i < count; i += nthreads) {
+                plans[i].reset(new perm_plan_s());
+                prep[i] = plan_prepare(&mats[i], &opts, *plans[i]);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthreads; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (std::thread &th : pool) th.join();
+    }
     std::map<std::pair<int, int>, BatchGroup> groups;
     std::vector<int> singles;
     for (int32_t i = 0; i < count; ++i) {
-        plans[i].reset(new perm_plan_s());
         perm_plan_s &P = *plans[i];
-        perm_status_t s = plan_prepare(&mats[i], &opts, P);
+        const perm_status_t s = prep[i];
         std::memset(&out[i], 0, sizeof(out[i]));
-        if (s != PERM_OK) { out[i].status = s; plans[i].reset(); continue; }
+        if (s != PERM_OK) {
+            out[i].status = s;
+            plans[i].reset();
+            fail(s, ("batch item " + std::to_string(i) + ": " + perm_status_string(s)).c_str());
+            continue;
+        }
         if (P.zero) { describe(P, &out[i]); out[i].status = PERM_OK; plans[i].reset(); continue; }
         if (P.m.n <= 8 || P.m.n > 48) { singles.push_back(i); continue; }
         groups[{nmax_bucket(P.m.n), P.limbs}].add(i, &P);

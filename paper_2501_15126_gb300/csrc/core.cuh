@@ -97,8 +97,10 @@ struct ArithF64 {
     typedef double P;   // a (partial) product
     typedef double V;   // a matrix value as stored
     struct Acc { double hi, lo; };
+    static constexpr bool kProdIsX = true;   // a product is itself a valid factor
     static __device__ __forceinline__ P one() { return 1.0; }
     static __device__ __forceinline__ P mul(P q, X x) { return q * x; }
+    static __device__ __forceinline__ P diff(P a, P b) { return a - b; }
     static __device__ __forceinline__ bool is_zero(P q) { return q == 0.0; }
     template <int S> static __device__ __forceinline__ X upd(X x, V v) { return S > 0 ? x + v : x - v; }
     static __device__ __forceinline__ X upd_rt(X x, V v, int s) { return fma((double)s, v, x); }
@@ -241,7 +243,9 @@ struct ArithExact {
         r.w[0] = 1;
         return r;
     }
+    static constexpr bool kProdIsX = false;
     static __device__ __forceinline__ P mul(const P &q, X x) { return ring_mul<L>(q, x); }
+    static __device__ __forceinline__ P diff(P a, const P &b) { ring_sub<L>(a, b); return a; }
     static __device__ __forceinline__ bool is_zero(const P &q) {
         u32 o = 0;
 #pragma unroll
@@ -387,11 +391,91 @@ __device__ __forceinline__ void rolled_block(Pol &pol, typename A::X (&x)[Pol::N
     }
 }
 
+// ------------------------------------------------------------------ two-state chains
+// Policies with kDual never apply column 0 to x.  A step's product is
+//     prod_i x_i = (column 0 off) ? A_1 : B_1,
+// where, over the rows of column 0 (group 0), A_m takes x_i and B_m takes
+// x_i + a_i0.  Group 0's rows are split by the next column that touches them
+// (S_m), and level m of both chains holds group m and S_m:
+//     A_m = A_{m+1} prod_{R_m} x prod_{S_m} x,
+//     B_m = B_{m+1} prod_{R_m} x prod_{S_m} (x + a_0),
+// so a flip of column j >= 1 rebuilds levels j..1 of both, and column 0's
+// steps cost nothing.  Steps 2p and 2p+1 of a block differ only in column 0
+// (off, then on, for even p; on, then off, for odd p), so the pair adds
+// (-1)^p (A_1 - B_1).  The flip before pair p is column 1 + ctz(p), sign bit
+// 1 + ctz(p) of p.  Every term is still the product of the same n numbers.
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ void dual_block(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&QA)[Bv + 1],
+                                           typename A::P (&QB)[Bv + 1], typename A::Blk &blk, int s_mid) {
+    static_assert(Bv >= 3, "the two-state block walks groups of two pairs");
+#pragma unroll 1
+    for (int p2 = 0; p2 < (1 << (Bv - 2)); ++p2) {
+        if (p2 != 0) {
+            const int p = p2 << 1;
+            const int j = __ffs(p);   // 1 + ctz(p), >= 2
+            const int s = (j == Bv - 1) ? s_mid : (((p >> j) & 1) ? -1 : 1);
+            pol.flip_dyn(j, x, s);
+#pragma unroll
+            for (int M = Bv - 1; M >= 1; --M)
+                if (M <= j) pol.level2(M, x, QA[M + 1], QB[M + 1], QA[M], QB[M]);
+        }
+        A::template blk_add<1>(blk, A::diff(QA[1], QB[1]));
+        pol.flip_dyn(1, x, (p2 & 1) ? -1 : 1);
+        pol.level2(1, x, QA[2], QB[2], QA[1], QB[1]);
+        A::template blk_add<-1>(blk, A::diff(QA[1], QB[1]));
+    }
+}
+
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
+    typedef typename A::X X;
+    typedef typename A::P P;
+    X x[Pol::NX];
+    const u64 g0 = q << K;
+    pol.init_x(x, g0 ^ (g0 >> 1));   // bit 0 of the code is 0: column 0 off
+    P QA, QB;
+    pol.chain_init2(x, QA, QB);
+    typename A::Acc acc = A::acc_zero();
+    typename A::Blk mid = A::blk_zero();
+    const u64 nblocks = 1ull << (K - Bv);
+    for (u64 h = 0; h < nblocks; ++h) {
+        if (h != 0 && (h & 7) == 0) {
+            A::acc_merge(acc, mid);
+            mid = A::blk_zero();
+        }
+        const u64 gb = g0 + (h << Bv);
+        if (h != 0) {
+            const int j = Bv + ctz64(h);
+            const int s = ((gb >> (j + 1)) & 1ull) ? -1 : 1;
+            pol.flip_dyn(j, x, s);
+            pol.chain_hi2(j, x, QA, QB);
+        }
+        const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
+        // the vote is also the warp's reconvergence point (see walk_chunk_single)
+        const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(QA) && A::is_zero(QB));
+        if (zero_skip && all_zero) {
+            pol.template flip_rt<Bv - 1>(x, s_mid);
+            ++skipped;
+            continue;
+        }
+        P LA[Bv + 1], LB[Bv + 1];
+        LA[Bv] = QA;
+        LB[Bv] = QB;
+#pragma unroll
+        for (int M = Bv - 1; M >= 1; --M) pol.level2(M, x, LA[M + 1], LB[M + 1], LA[M], LB[M]);
+        typename A::Blk blk = A::blk_zero();
+        dual_block<Pol, A, Bv>(pol, x, LA, LB, blk, s_mid);
+        A::blk_accumulate(mid, blk);
+    }
+    A::acc_merge(acc, mid);
+    return acc;
+}
+
 // ------------------------------------------------------------------ one chunk
 // Walks Gray indices [q 2^K, (q+1) 2^K) and returns sum (-1)^g prod_i x_i(g).
 
 template <class Pol, class A, int Bv>
-__device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
+__device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
     typedef typename A::X X;
     typedef typename A::P P;
     X x[Pol::NX];
@@ -445,6 +529,12 @@ __device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, in
     }
     A::acc_merge(acc, mid);
     return acc;
+}
+
+template <class Pol, class A, int Bv>
+__device__ __forceinline__ typename A::Acc walk_chunk(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
+    if constexpr (Pol::kDual) return walk_chunk_dual<Pol, A, Bv>(pol, q, K, zero_skip, skipped);
+    else return walk_chunk_single<Pol, A, Bv>(pol, q, K, zero_skip, skipped);
 }
 
 // ------------------------------------------------------------------ persistent warp loop

@@ -60,16 +60,20 @@ struct BatchArgs {
 // path: values doubled).  Slots are numbered group by group (a row's group is
 // the first column position that touches it), so group m is the contiguous
 // slot range [gbegin[m], gbegin[m+1]); group 0 is exactly column 0's rows.
-// For NMAX in {16, 32, 48} the header is 32 + 11 NMAX bytes, a multiple of 16.
+// Group 0 is sorted by the next column that touches each of its rows: S_m,
+// the rows of column 0 next touched by column m, are the contiguous slots
+// [sbegin[m], sbegin[m+1]).  For NMAX in {16, 32, 48} the header is
+// 48 + 12 NMAX bytes, a multiple of 16.
 template <int NMAX, typename V>
 struct DevMat {
     int n;                              // dimension
-    int top;                            // highest nonempty row group
+    int top;                            // highest m with group m or S_m nonempty
     int nnz;                            // values stored (columns 0..n-2)
     int bytes;                          // size of this image, a multiple of 16
     unsigned long long colmask[NMAX];   // slots touched by column position p (p < n-1)
     unsigned short colptr[NMAX];        // first value of column p
     unsigned char gbegin[NMAX + 16];    // first slot of group m (m <= n; gbegin[n] = n)
+    unsigned char sbegin[NMAX + 16];    // first slot of S_m (1 <= m <= n; sbegin[n] = |group 0|)
     V x0[NMAX];                         // Nijenhuis-Wilf start values by slot
     V val[NMAX * NMAX];                 // nnz values, column after column
 };

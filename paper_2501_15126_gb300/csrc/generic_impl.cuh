@@ -62,6 +62,11 @@ struct GenericPol {
     static constexpr int Bv = PERM_GENERIC_B;
     static constexpr bool kPaired = false;
     static constexpr bool kRolled = true;
+    // Two-state chains (core.cuh) where a group's product can be shared by
+    // both chains (FP64); ring products cannot, so the exact walks keep one
+    // chain and apply column 0 (pair_terms).  At 48 slots the second chain's
+    // registers would spill x, so that bucket keeps one chain too.
+    static constexpr bool kDual = A::kProdIsX && NMAX <= 32;
     typedef typename A::X X;
     typedef typename A::P P;
     typedef typename A::V V;
@@ -70,10 +75,12 @@ struct GenericPol {
 
     const M *m;
     P Qh[NMAX + 1];     // chain levels >= B (dynamic index: local memory)
+    P Bh[kDual ? NMAX + 1 : 1];   // the same levels of the column-0-on chain
 
     __device__ __forceinline__ explicit GenericPol(const M *mat) : m(mat) {}
 
     __device__ __forceinline__ int gbegin(int g) const { return ((const volatile unsigned char *)m->gbegin)[g]; }
+    __device__ __forceinline__ int sbegin(int g) const { return ((const volatile unsigned char *)m->sbegin)[g]; }
     __device__ __forceinline__ Mask colmask(int j) const { return (Mask)((const volatile u64 *)m->colmask)[j]; }
     __device__ __forceinline__ const volatile V *colvals(int j) const {
         return m->val + ((const volatile unsigned short *)m->colptr)[j];
@@ -171,6 +178,68 @@ struct GenericPol {
         }
         A::template blk_add<1>(blk, p0);
         A::template blk_add<-1>(blk, p1);
+    }
+
+    // qa *= x[k], qb *= x[k] + a_k0 for the rows k in [b, e) of column 0
+    // (b < e), highest slot first; column 0's values are the image's first
+    __device__ __forceinline__ void dual_range(const X (&x)[NX], int b, int e, P &qa, P &qb) const {
+        const volatile V *v = m->val;
+        switch (e) {
+#define PERM_DUAL_CASE(k)                                             \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            qa = A::mul(qa, x[k]);                                    \
+            qb = A::mul(qb, A::template upd<1>(x[k], v[k]));          \
+            if (k <= b) break;                                        \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_DUAL_CASE)
+#undef PERM_DUAL_CASE
+        default: break;
+        }
+    }
+    // level g of both chains from level g+1: group g, then S_g
+    __device__ __forceinline__ void level2(int g, const X (&x)[NX], P qa_in, P qb_in, P &qa, P &qb) const {
+        const int b = gbegin(g), e = gbegin(g + 1);
+        if (b < e) {
+            if constexpr (A::kProdIsX) {
+                const P t = prod_range(x, b, e, A::one());
+                qa = A::mul(qa_in, t);
+                qb = A::mul(qb_in, t);
+            } else {
+                qa = prod_range(x, b, e, qa_in);
+                qb = prod_range(x, b, e, qb_in);
+            }
+        } else {
+            qa = qa_in;
+            qb = qb_in;
+        }
+        const int sb = sbegin(g), se = sbegin(g + 1);
+        if (sb < se) dual_range(x, sb, se, qa, qb);
+    }
+    // both chains, all levels from the top down to B
+    __device__ __forceinline__ void chain_init2(const X (&x)[NX], P &QA, P &QB) {
+        const int top = m->top;
+        P qa = A::one(), qb = A::one();
+        for (int g = NMAX; g > top; --g) { Qh[g] = qa; Bh[g] = qb; }
+        for (int g = top; g >= Bv; --g) {
+            level2(g, x, qa, qb, qa, qb);
+            Qh[g] = qa;
+            Bh[g] = qb;
+        }
+        QA = qa;
+        QB = qb;
+    }
+    // after a flip of column j >= B: levels j..B of both chains
+    __device__ __forceinline__ void chain_hi2(int j, const X (&x)[NX], P &QA, P &QB) {
+        P qa = Qh[j + 1], qb = Bh[j + 1];
+        for (int g = j; g >= Bv; --g) {
+            level2(g, x, qa, qb, qa, qb);
+            Qh[g] = qa;
+            Bh[g] = qb;
+        }
+        QA = qa;
+        QB = qb;
     }
 
     // x = x0 + sum of the columns set in Gray code G (columns < n-1 only);

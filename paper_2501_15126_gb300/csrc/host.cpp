@@ -167,19 +167,50 @@ Layout make_layout(const Matrix &m, const int *col_order, int ordering) {
     }
     for (int i = 0; i < n; ++i)
         if (!seen[i]) order_seen[nseen++] = i;   // empty rows (perm is 0 anyway)
-    // slots: stable by group, inside a group in first-touch order
-    int slot = 0;
-    for (int g = 0; g < n; ++g) {
-        L.group_begin[g] = slot;
-        for (int k = 0; k < n; ++k) {
-            const int r = order_seen[k];
-            if (first[r] == g) { L.row_order[slot] = r; L.slot_of_row[r] = slot; L.group_of_slot[slot] = g; ++slot; }
-        }
+    // column 0's rows (group 0): their first touching position after 0
+    // (n-1 when no flipped column touches them again)
+    int second[kNMax];
+    for (int i = 0; i < n; ++i) {
+        second[i] = n - 1;
+        if (first[i] != 0) continue;
+        for (int p = 1; p < n - 1; ++p)
+            if ((m.colmask[col_order[p]] >> i) & 1ull) { second[i] = p; break; }
     }
-    L.group_begin[n] = slot;
+    // slots: stable by group, inside a group in first-touch order, except
+    // that group 0 is sorted by the second touching position (so each set S_m
+    // below is a contiguous slot range)
+    int by_group[kNMax], gcount[kNMax + 1] = {};
+    for (int i = 0; i < n; ++i) ++gcount[first[i] + 1];
+    for (int g = 0; g < n; ++g) gcount[g + 1] += gcount[g];
+    for (int g = 0; g <= n; ++g) L.group_begin[g] = gcount[g];
+    for (int k = 0; k < n; ++k) {   // counting sort by group, stable in first-touch order
+        const int r = order_seen[k];
+        by_group[gcount[first[r]]++] = r;
+    }
+    std::stable_sort(by_group, by_group + L.group_begin[1], [&](int a, int b) { return second[a] < second[b]; });
+    for (int slot = 0; slot < n; ++slot) {
+        const int r = by_group[slot];
+        L.row_order[slot] = r;
+        L.slot_of_row[r] = slot;
+        L.group_of_slot[slot] = first[r];
+    }
     L.top = 0;
     for (int g = 0; g < n; ++g)
         if (L.group_begin[g + 1] > L.group_begin[g]) L.top = g;
+    // S_m = rows of column 0 whose next touching position is m: slots
+    // [s_begin[m], s_begin[m+1]) inside [0, group_begin[1])
+    for (int mm = 0; mm <= n; ++mm) L.s_begin[mm] = 0;
+    {
+        int k = 0;
+        for (int mm = 1; mm <= n - 1; ++mm) {
+            L.s_begin[mm] = k;
+            while (k < L.group_begin[1] && second[L.row_order[k]] == mm) ++k;
+        }
+        L.s_begin[n] = k;
+    }
+    L.top_dual = L.top;
+    for (int mm = 1; mm <= n - 1; ++mm)
+        if (L.s_begin[mm + 1] > L.s_begin[mm]) L.top_dual = std::max(L.top_dual, mm);
     for (int p = 0; p < n; ++p) {
         uint64_t rows = m.colmask[col_order[p]], mask = 0;
         while (rows) {
@@ -221,6 +252,24 @@ double cost_per_step_paired(const Layout &L) {
     const double w0 = std::ldexp(1.0, n - 2) / steps;           // column-0 steps = pairs
     const double pair_ops = r0 == 1 ? 2.0 : 3.0 * r0 - 1.0;
     return total + w0 * pair_ops;
+}
+
+double cost_per_step_dual(const Layout &L, bool shared_product) {
+    const int n = L.n;
+    if (n < 3) return cost_per_step(L, false);
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    double total = 0.0, rate = 0.0;
+    for (int m = n - 2; m >= 1; --m) {
+        const double w = std::ldexp(1.0, n - m - 2) / steps;   // Lemma 2: column m's flips per step
+        total += w * L.col_nnz[m];
+        rate += w;                                             // level m is rebuilt by any column >= m
+        const int r = L.group_begin[m + 1] - L.group_begin[m];
+        const int sm = L.s_begin[m + 1] - L.s_begin[m];
+        const double level = (shared_product ? (r ? r + 2.0 : 0.0) : 2.0 * r) + 3.0 * sm;
+        total += rate * level;
+    }
+    const double w0 = std::ldexp(1.0, n - 2) / steps;         // pairs of steps
+    return total + w0 * 2.0;
 }
 
 Layout choose_layout(const Matrix &m, int ordering_opt) {
@@ -269,6 +318,15 @@ void partition_alg4(const Layout &L, double gr_ratio, int base_regs, int *k_out,
     *c_out = c;
 }
 
+// log2(r!) for a row or column count r <= 64, summed directly (no lgamma:
+// it writes a process-wide sign variable, and plans are prepared on several
+// threads).
+static double log2_factorial(int r) {
+    double s = 0.0;
+    for (int k = 2; k <= r; ++k) s += std::log2((double)k);
+    return s;
+}
+
 double bound_log2(const Matrix &m) {
     const int n = m.n;
     bool binary = true;
@@ -284,8 +342,8 @@ double bound_log2(const Matrix &m) {
         }
         if (rs == 0.0 || cs == 0.0) return -INFINITY;
         if (binary) {
-            rows += std::lgamma(rs + 1.0) / rs / std::log(2.0);   // Bregman-Minc
-            cols += std::lgamma(cs + 1.0) / cs / std::log(2.0);
+            rows += log2_factorial((int)rs) / rs;   // Bregman-Minc
+            cols += log2_factorial((int)cs) / cs;
         } else {
             rows += std::log2(rs);
             cols += std::log2(cs);

@@ -61,6 +61,11 @@ struct Layout {
     uint64_t colmask[kNMax] = {};  // by position p: slots touched by that column
     int col_nnz[kNMax] = {};
     int top = 0;                   // highest nonempty group
+    // Column 0's rows (group 0, slots [0, group_begin[1])) split by the next
+    // position that touches them: S_m = slots [s_begin[m], s_begin[m+1]),
+    // m = 1..n-1 (m = n-1: no flipped column touches them again).
+    int s_begin[kNMax + 1] = {};
+    int top_dual = 0;              // highest m with group m or S_m nonempty
 };
 
 // Column orders.  PAPER is Algorithm 3; its row order is returned too.
@@ -98,6 +103,10 @@ double bound_log2(const Matrix &m);
 // Smallest w in 1..3 with the doubled-NW sum recoverable modulo 2^(64 w),
 // or 0 when even w = 3 is not enough.
 int exact_words_for(double bound, int n);
+// Operations per Gray step of the generic kernels' two-state chains (column 0
+// folded into a second chain): flips of columns >= 1, the levels they
+// rebuild, and one difference and accumulation per pair of steps.
+double cost_per_step_dual(const Layout &L, bool shared_product);
 // The fewest 32-bit limbs (2..6) of a ring that holds 2^(n-1) perm with sign
 // and margin, or 0.
 int exact_limbs_for(double bound, int n);
