@@ -201,6 +201,14 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
             const int l = exact_limbs_for(b, n);
             if (l && (l + 1) / 2 == P.arith) P.limbs = l;
         }
+        // |x_i| <= sum_j |a_ij| at every Gray index: four factors <= 127 fit 32 bits
+        int64_t max_row = 0;
+        for (int i = 0; i < n; ++i) {
+            int64_t rs = 0;
+            for (int j = 0; j < n; ++j) rs += P.m.ival(i, j) < 0 ? -P.m.ival(i, j) : P.m.ival(i, j);
+            max_row = std::max(max_row, rs);
+        }
+        P.fold = max_row <= 127;
     }
     P.ms_plan = now_ms() - t0;
     return PERM_OK;
@@ -273,7 +281,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
     P.words = P.arith == 0 ? 2 : P.arith;
 
     if (engine == PERM_ENGINE_GENERIC) {
-        P.gf = generic_fns(nmax, P.limbs);
+        P.gf = generic_fns(nmax, P.kind());
         if (!P.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this size");
         P.nmax = nmax;
         std::vector<unsigned char> img;

@@ -38,11 +38,11 @@ int batch_chunk_log2(int n, int B, int K_target) {
     return std::min(K, n - 1);
 }
 
-int BatchGroup::setup(int nmax_, int limbs_, int K_target) {
+int BatchGroup::setup(int nmax_, int kind_, int K_target) {
     nmax = nmax_;
-    limbs = limbs_;
-    arith = (limbs + 1) / 2;
-    gf = generic_fns(nmax, limbs);
+    kind = kind_;
+    arith = ((kind >> 1) + 1) / 2;
+    gf = generic_fns(nmax, kind);
     if (!gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this group");
     words = arith == 0 ? 2 : arith;
     // task table
@@ -204,7 +204,7 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
         }
         if (P.zero) { describe(P, &out[i]); out[i].status = PERM_OK; plans[i].reset(); continue; }
         if (P.m.n <= 8 || P.m.n > 48) { singles.push_back(i); continue; }
-        groups[{nmax_bucket(P.m.n), P.limbs}].add(i, &P);
+        groups[{nmax_bucket(P.m.n), P.kind()}].add(i, &P);
     }
     const double t_prep = now_ms() - t0;
 
@@ -218,8 +218,8 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
         if (!K_target) {
             if (!chunk_log2_is_tuned(kv.first.first, kv.first.second)) {
                 G.nmax = kv.first.first;
-                G.limbs = kv.first.second;
-                G.arith = (G.limbs + 1) / 2;
+                G.kind = kv.first.second;
+                G.arith = ((G.kind >> 1) + 1) / 2;
                 autotune_group(G, st);
             }
             K_target = tuned_chunk_log2(kv.first.first, kv.first.second);

@@ -17,10 +17,10 @@ namespace perm {
 // lowered so that the matrix still fills a 32-lane task, never below B.
 int batch_chunk_log2(int n, int B, int K_target);
 
-// The autotuned chunk target of a (NMAX, arithmetic) family (tune.cpp);
-// the arithmetic is 0 (FP64) or the exact ring's limb count.
-int tuned_chunk_log2(int nmax, int limbs);
-bool chunk_log2_is_tuned(int nmax, int limbs);
+// The autotuned chunk target of a (NMAX, kernel family) pair (tune.cpp); the
+// family is perm_plan_s::kind().
+int tuned_chunk_log2(int nmax, int kind);
+bool chunk_log2_is_tuned(int nmax, int kind);
 struct BatchGroup;
 int autotune_group(const BatchGroup &group, cudaStream_t st);
 
@@ -28,7 +28,7 @@ int autotune_group(const BatchGroup &group, cudaStream_t st);
 struct BatchGroup {
     std::vector<int> idx;                 // positions in the caller's array
     std::vector<perm_plan_s *> plans;
-    int nmax = 0, limbs = 0, arith = 0, words = 2;   // limbs: 0 = FP64, else the exact ring's 32-bit limbs
+    int nmax = 0, kind = 0, arith = 0, words = 2;   // kind: generic kernel family (perm_plan_s::kind())
     GenericFns gf;
     std::vector<pk::BatchMat> mats;
     std::vector<unsigned char> images;
@@ -41,7 +41,7 @@ struct BatchGroup {
     uint64_t *d_task_out = nullptr, *d_result = nullptr, *d_counters = nullptr;
 
     void add(int i, perm_plan_s *p) { idx.push_back(i); plans.push_back(p); }
-    int setup(int nmax, int limbs, int K_target);   // perm_status_t
+    int setup(int nmax, int kind, int K_target);   // perm_status_t
     size_t arena_bytes() const;
     void bind(unsigned char *base);
     int upload(cudaStream_t st);

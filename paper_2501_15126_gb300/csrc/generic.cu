@@ -81,20 +81,21 @@ cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, u
 }
 
 GenericFns generic_fns_f64(int nmax);
-GenericFns generic_fns_r64(int nmax);
-GenericFns generic_fns_r96(int nmax);
-GenericFns generic_fns_r128(int nmax);
-GenericFns generic_fns_r160(int nmax);
-GenericFns generic_fns_r192(int nmax);
+GenericFns generic_fns_r64(int nmax, int fold);
+GenericFns generic_fns_r96(int nmax, int fold);
+GenericFns generic_fns_r128(int nmax, int fold);
+GenericFns generic_fns_r160(int nmax, int fold);
+GenericFns generic_fns_r192(int nmax, int fold);
 
-GenericFns generic_fns(int nmax, int limbs) {
+GenericFns generic_fns(int nmax, int kind) {
+    const int limbs = kind >> 1, fold = kind & 1;
     switch (limbs) {
-    case 0: return generic_fns_f64(nmax);
-    case 2: return generic_fns_r64(nmax);
-    case 3: return generic_fns_r96(nmax);
-    case 4: return generic_fns_r128(nmax);
-    case 5: return generic_fns_r160(nmax);
-    case 6: return generic_fns_r192(nmax);
+    case 0: return fold ? GenericFns() : generic_fns_f64(nmax);
+    case 2: return generic_fns_r64(nmax, fold);
+    case 3: return generic_fns_r96(nmax, fold);
+    case 4: return generic_fns_r128(nmax, fold);
+    case 5: return generic_fns_r160(nmax, fold);
+    case 6: return generic_fns_r192(nmax, fold);
     default: return GenericFns();
     }
 }

@@ -56,6 +56,14 @@ template <int NMAX> struct SlotMask { typedef u64 T; static __device__ __forcein
 template <> struct SlotMask<16> { typedef u32 T; static __device__ __forceinline__ int low(T v) { return __ffs((int)v) - 1; } };
 template <> struct SlotMask<32> { typedef u32 T; static __device__ __forceinline__ int low(T v) { return __ffs((int)v) - 1; } };
 
+// Exact arithmetic with folded products: for matrices whose rows have
+// absolute sums <= 127 every |x_i| is <= 127, so four consecutive factors
+// multiply exactly in 32 bits (127^4 < 2^28) and one ring multiplication
+// takes all four.  The fold blocks are fixed slot quadruples [4t, 4t+3].
+template <int NL> struct ArithExactFold : ArithExact<NL> {};
+template <class A> struct FoldOf { static constexpr bool v = false; };
+template <int NL> struct FoldOf<ArithExactFold<NL>> { static constexpr bool v = true; };
+
 template <int NMAX, class A>
 struct GenericPol {
     static constexpr int NX = NMAX;
@@ -100,6 +108,7 @@ struct GenericPol {
     }
     // q * x[b] * ... * x[e-1] (b < e), highest slot first
     __device__ __forceinline__ static P prod_range(const X (&x)[NX], int b, int e, P q) {
+        if constexpr (FoldOf<A>::v) return prod_range_folded(x, b, e, q);
         switch (e) {
 #define PERM_PROD_CASE(k)                                             \
     case k + 1:                                                       \
@@ -113,6 +122,58 @@ struct GenericPol {
         default: break;
         }
         return q;
+    }
+    // the same with the factors of each slot quadruple multiplied in 32 bits
+    // first (FoldOf<A>): a quadruple starts at k = 4t+3 and folds at k = 4t
+    // or where the range ends
+    __device__ __forceinline__ static P prod_range_folded(const X (&x)[NX], int b, int e, P q) {
+        int t = 1;
+        switch (e) {
+#define PERM_FPROD_CASE(k)                                            \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            if constexpr (k % 4 == 3) t = x[k];                       \
+            else t *= x[k];                                           \
+            if constexpr (k % 4 == 0) {                               \
+                q = A::mul(q, t);                                     \
+                if (k <= b) break;                                    \
+            } else if (k <= b) {                                      \
+                q = A::mul(q, t);                                     \
+                break;                                                \
+            }                                                         \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_FPROD_CASE)
+#undef PERM_FPROD_CASE
+        default: break;
+        }
+        return q;
+    }
+    // x[b] * ... * x[e-1] (b < e): one jump to the first factor, then the
+    // ladder (no multiplication by 1)
+    __device__ __forceinline__ static P prod_range1(const X (&x)[NX], int b, int e) {
+        P t = A::one();
+        switch (e) {
+#define PERM_ENTRY_CASE(k)                                            \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            t = x[k];                                                 \
+            if (k <= b) return t;                                     \
+        }                                                             \
+        goto perm_step_##k;
+            PERM_SLOT_CASES_DOWN(PERM_ENTRY_CASE)
+#undef PERM_ENTRY_CASE
+        default: return t;
+        }
+#define PERM_STEP_CASE(k)                                             \
+    perm_step_##k:                                                    \
+        if constexpr (k >= 1 && k <= NMAX) {                          \
+            t = A::mul(t, x[k - 1]);                                  \
+            if (k - 1 <= b) return t;                                 \
+        }
+        PERM_SLOT_CASES_DOWN(PERM_STEP_CASE)
+#undef PERM_STEP_CASE
+        return t;
     }
     // x[k] += s * w[k - b] for k in [b, e) (b < e), highest slot first
     __device__ __forceinline__ static void add_range(X (&x)[NX], int b, int e, const volatile V *w, int s) {
@@ -161,6 +222,10 @@ struct GenericPol {
     // multiplies the rows before the flip, applies it, and multiplies after.
     template <int S>
     __device__ __forceinline__ void pair_terms(X (&x)[NX], P q1, typename A::Blk &blk) {
+        if constexpr (FoldOf<A>::v) {
+            pair_terms_folded<S>(x, q1, blk);
+            return;
+        }
         const volatile V *v = m->val;
         P p0 = q1, p1 = q1;
         switch (gbegin(1)) {
@@ -174,6 +239,39 @@ struct GenericPol {
         [[fallthrough]];
             PERM_SLOT_CASES_DOWN(PERM_PAIR_CASE)
 #undef PERM_PAIR_CASE
+        default: break;
+        }
+        A::template blk_add<1>(blk, p0);
+        A::template blk_add<-1>(blk, p1);
+    }
+
+    // pair_terms with folded products (slot quadruples, as prod_range_folded)
+    template <int S>
+    __device__ __forceinline__ void pair_terms_folded(X (&x)[NX], P q1, typename A::Blk &blk) {
+        const volatile V *v = m->val;
+        P p0 = q1, p1 = q1;
+        int t0 = 1, t1 = 1;
+        switch (gbegin(1)) {
+#define PERM_FPAIR_CASE(k)                                            \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            const X xo = x[k];                                        \
+            x[k] = A::template upd<S>(xo, v[k]);                      \
+            if constexpr (k % 4 == 3) {                               \
+                t0 = xo;                                              \
+                t1 = x[k];                                            \
+            } else {                                                  \
+                t0 *= xo;                                             \
+                t1 *= x[k];                                           \
+            }                                                         \
+            if constexpr (k % 4 == 0) {                               \
+                p0 = A::mul(p0, t0);                                  \
+                p1 = A::mul(p1, t1);                                  \
+            }                                                         \
+        }                                                             \
+        [[fallthrough]];
+            PERM_SLOT_CASES_DOWN(PERM_FPAIR_CASE)
+#undef PERM_FPAIR_CASE
         default: break;
         }
         A::template blk_add<1>(blk, p0);
@@ -203,7 +301,7 @@ struct GenericPol {
         const int b = gbegin(g), e = gbegin(g + 1);
         if (b < e) {
             if constexpr (A::kProdIsX) {
-                const P t = prod_range(x, b, e, A::one());
+                const P t = prod_range1(x, b, e);
                 qa = A::mul(qa_in, t);
                 qb = A::mul(qb_in, t);
             } else {
@@ -437,6 +535,28 @@ static GenericFns make_fns() {
         case 16: return make_fns<16, ARITH>();                           \
         case 32: return make_fns<32, ARITH>();                           \
         case 48: return make_fns<48, ARITH>();                           \
+        default: return GenericFns();                                    \
+        }                                                                \
+    }                                                                    \
+    }
+
+// Defines perm::generic_fns_<NAME>(nmax, fold) for one exact ring width,
+// with (fold = 1) and without folded products.
+#define PERM_GENERIC_EXACT_UNIT(NAME, NL)                                \
+    namespace perm {                                                     \
+    GenericFns generic_fns_##NAME(int nmax, int fold) {                  \
+        if (fold) {                                                      \
+            switch (nmax) {                                              \
+            case 16: return make_fns<16, pk::ArithExactFold<NL>>();      \
+            case 32: return make_fns<32, pk::ArithExactFold<NL>>();      \
+            case 48: return make_fns<48, pk::ArithExactFold<NL>>();      \
+            default: return GenericFns();                                \
+            }                                                            \
+        }                                                                \
+        switch (nmax) {                                                  \
+        case 16: return make_fns<16, pk::ArithExact<NL>>();              \
+        case 32: return make_fns<32, pk::ArithExact<NL>>();              \
+        case 48: return make_fns<48, pk::ArithExact<NL>>();              \
         default: return GenericFns();                                    \
         }                                                                \
     }                                                                    \

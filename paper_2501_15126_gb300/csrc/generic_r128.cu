@@ -2,4 +2,4 @@
 #define PERM_GENERIC_B 5
 #include "generic_impl.cuh"
 
-PERM_GENERIC_UNIT(r128, pk::ArithExact<4>)
+PERM_GENERIC_EXACT_UNIT(r128, 4)

@@ -2,4 +2,4 @@
 #define PERM_GENERIC_B 5
 #include "generic_impl.cuh"
 
-PERM_GENERIC_UNIT(r96, pk::ArithExact<3>)
+PERM_GENERIC_EXACT_UNIT(r96, 3)

@@ -20,8 +20,10 @@ struct GenericFns {
     size_t devmat_bytes = 0;   // the largest possible image (every value stored)
 };
 
-// limbs: 0 = FP64, 2..6 = exact modulo 2^(32 limbs).  nmax in {16, 32, 48}.
-GenericFns generic_fns(int nmax, int limbs);
+// kind = 2 limbs + fold: limbs 0 = FP64, 2..6 = exact modulo 2^(32 limbs);
+// fold = 1 selects the exact kernels that multiply slot quadruples in 32 bits
+// first (every row's absolute sum <= 127).  nmax in {16, 32, 48}.
+GenericFns generic_fns(int nmax, int kind);
 
 // Per-matrix sums of a multi-matrix walk: result[m] = sum of task results
 // [mats[m].task_begin, mats[m+1].task_begin) (the last ends at ntasks), in a

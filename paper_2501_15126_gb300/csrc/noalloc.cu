@@ -87,7 +87,7 @@ extern "C" perm_status_t perm_compute_noalloc(const perm_matrix_t *A, const perm
     if (P.zero) { describe(P, out); out->status = PERM_OK; return PERM_OK; }
     const int nmax = nmax_bucket(n);
     P.nmax = nmax;
-    P.gf = generic_fns(nmax, P.limbs);
+    P.gf = generic_fns(nmax, P.kind());
     if (!P.gf.walk) { out->status = PERM_ERR_INTERNAL; return fail(PERM_ERR_INTERNAL, "no generic kernel"); }
     const size_t img_bytes = devmat_bytes_for(P.L, P.arith, nmax);
     if (img_bytes > kOffTasks - kOffImage) { out->status = PERM_ERR_INTERNAL; return fail(PERM_ERR_INTERNAL, "image too large"); }

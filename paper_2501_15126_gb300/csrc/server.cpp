@@ -101,7 +101,7 @@ struct RangeAlloc {
 };
 
 struct Family {
-    int nmax = 0, limbs = 0, arith = 0, words = 2, K_target = 14;   // limbs: 0 = FP64, else the exact ring's
+    int nmax = 0, kind = 0, arith = 0, words = 2, K_target = 14;   // kind: generic kernel family
     GenericFns gf;
     int grid_max = 1;
     unsigned char *d_images = nullptr;
@@ -167,7 +167,7 @@ struct perm_server_s {
     double t_first = 0.0, t_last = 0.0;
     perm_status_t init_status = PERM_OK;
 
-    static int family_index(int nmax, int limbs) { return (nmax / 16 - 1) * 7 + limbs; }
+    static int family_index(int nmax, int kind) { return (nmax / 16 - 1) * 14 + kind; }
 
     perm_status_t init_device() {
         cudaError_t e = cudaSetDevice(device);
@@ -189,21 +189,21 @@ struct perm_server_s {
             if ((e = cudaMallocHost(&f.h_res, 32 * (size_t)maxn)) != cudaSuccess) return cuda_fail(e, "pinned");
             if ((e = cudaMalloc(&f.d_res, 32 * (size_t)maxn)) != cudaSuccess) return cuda_fail(e, "res");
         }
-        fam.resize(21);
+        fam.resize(42);
         return PERM_OK;
     }
 
-    perm_status_t ensure_family(int fi, int nmax, int limbs) {
+    perm_status_t ensure_family(int fi, int nmax, int kind) {
         Family &F = fam[fi];
         if (F.ready) return PERM_OK;
         cudaSetDevice(device);
         F.nmax = nmax;
-        F.limbs = limbs;
-        F.arith = (limbs + 1) / 2;
+        F.kind = kind;
+        F.arith = ((kind >> 1) + 1) / 2;
         F.words = F.arith == 0 ? 2 : F.arith;
-        F.gf = generic_fns(nmax, limbs);
+        F.gf = generic_fns(nmax, kind);
         if (!F.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this family");
-        F.K_target = tuned_chunk_log2(nmax, limbs);
+        F.K_target = tuned_chunk_log2(nmax, kind);
         int bps = 0;
         cudaError_t e = F.gf.occ(256, F.gf.devmat_bytes, &bps);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy");
@@ -637,8 +637,8 @@ perm_status_t perm_submit(perm_server_t s, const perm_matrix_t *A, uint64_t *tic
     }
     if (P.m.n > 8 && P.m.n <= 48) {
         const int nmax = nmax_bucket(P.m.n);
-        raw->family = perm_server_s::family_index(nmax, P.limbs);
-        st = s->ensure_family(raw->family, nmax, P.limbs);
+        raw->family = perm_server_s::family_index(nmax, P.kind());
+        st = s->ensure_family(raw->family, nmax, P.kind());
         if (st != PERM_OK) { s->all.erase(raw->ticket); return st; }
     }
     s->queue.push_back(raw);

@@ -28,26 +28,26 @@ constexpr size_t kSampleMats = 256;
 constexpr size_t kMinMatsToTune = 64;
 }  // namespace
 
-int tuned_chunk_log2(int nmax, int limbs) {
+int tuned_chunk_log2(int nmax, int kind) {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_choice.find({nmax, limbs});
+    auto it = g_choice.find({nmax, kind});
     return it != g_choice.end() ? it->second : kDefaultK;
 }
 
-bool chunk_log2_is_tuned(int nmax, int limbs) {
+bool chunk_log2_is_tuned(int nmax, int kind) {
     std::lock_guard<std::mutex> lk(g_mu);
-    return g_choice.count({nmax, limbs}) > 0;
+    return g_choice.count({nmax, kind}) > 0;
 }
 
-void set_tuned_chunk_log2(int nmax, int limbs, int K) {
+void set_tuned_chunk_log2(int nmax, int kind, int K) {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_choice[{nmax, limbs}] = K;
+    g_choice[{nmax, kind}] = K;
 }
 
 // Times `group` restricted to an evenly spaced sample of its matrices at each
 // candidate K on `st`, and records the fastest.  Returns the chosen K.
 int autotune_group(const BatchGroup &group, cudaStream_t st) {
-    if (group.plans.size() < kMinMatsToTune) return tuned_chunk_log2(group.nmax, group.limbs);
+    if (group.plans.size() < kMinMatsToTune) return tuned_chunk_log2(group.nmax, group.kind);
     BatchGroup sample;
     const size_t step = std::max<size_t>(1, group.plans.size() / kSampleMats);
     for (size_t i = 0; i < group.plans.size() && sample.plans.size() < kSampleMats; i += step)
@@ -58,7 +58,7 @@ int autotune_group(const BatchGroup &group, cudaStream_t st) {
     int best_k = kDefaultK;
     float best_ms = 1e30f;
     for (int K : kCandidates) {
-        if (sample.setup(group.nmax, group.limbs, K) != PERM_OK) continue;
+        if (sample.setup(group.nmax, group.kind, K) != PERM_OK) continue;
         DeviceArena arena;
         if (arena.alloc(sample.arena_bytes()) != cudaSuccess) continue;
         sample.bind(arena.base);
@@ -75,7 +75,7 @@ int autotune_group(const BatchGroup &group, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
-    set_tuned_chunk_log2(group.nmax, group.limbs, best_k);
+    set_tuned_chunk_log2(group.nmax, group.kind, best_k);
     return best_k;
 }
 

@@ -139,6 +139,38 @@ def test_odd_limb_rings_give_closed_forms_exactly(engine):
         assert A.permanent(a, engine=engine, exact_words=(limbs + 1) // 2).value == want, (n, sign)
 
 
+@pytest.mark.parametrize("max_row", [127, 128, 900])
+def test_folded_and_unfolded_exact_products(max_row):
+    """Exact generic walks multiply slot quadruples in 32 bits first when every
+    row's absolute sum is <= 127, and factor by factor otherwise; both sides of
+    the boundary (and large entries) match the oracle bit for bit."""
+    a = rand_pattern(17, 0.45, 21, "int")
+    row = np.abs(a).sum(axis=1)
+    i = int(np.argmax(row))
+    a[i, i] += max_row - int(row[i]) if a[i, i] >= 0 else -(max_row - int(row[i]))
+    assert int(np.abs(a).sum(axis=1).max()) == max_row
+    want = oracle.ryser_gray(a)
+    for K in (0, 5, 9):
+        r = A.permanent(a, engine=A.PERM_ENGINE_GENERIC, chunk_log2=K)
+        assert r.value == want, (max_row, K)
+
+
+def test_ill_conditioned_f64_stays_within_the_terms_bound():
+    """A sparse (0,1] matrix whose permanent (9.7e-10) is 1.6e6 times smaller
+    than the sum of its |Nijenhuis-Wilf terms|: relative to the permanent no
+    FP64 summation order guarantees 1e-9, so the check is the absolute one,
+    |error| <= 1e-12 sum|terms| (above 64 n u sum|terms|), on every engine
+    and chunk length."""
+    a = synth.single_er(17, 0.1, 532, values="f64")
+    want, absum = oracle.nw_perm(a, threads=8)
+    want, absum = float(want), float(absum)
+    assert absum / abs(want) > 1e6
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        for K in (0, 5, 10):
+            r = A.permanent(a, engine=engine, chunk_log2=K)
+            assert abs(r.value - want) <= 1e-12 * absum, (engine, K, r.value, want)
+
+
 def test_exact_negative_entries():
     a = rand_pattern(18, 0.35, 4, "int")
     assert A.permanent(a).value == oracle.ryser_gray(a)
