@@ -169,7 +169,6 @@ struct Emitter {
         o << "struct GenPol {\n";
         o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
         o << "    static constexpr bool kPaired = " << (P.arith == 0 ? "true" : "false") << ";\n";
-        o << "    static constexpr bool kRolled = false;\n";
         o << "    static constexpr bool kDual = false;\n";
         o << "    typedef A::X X;\n    typedef A::P P;\n";
         o << "    X *xg;\n    unsigned long long stride;\n";

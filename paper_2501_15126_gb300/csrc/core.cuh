@@ -26,10 +26,11 @@
 // persistent grid take tasks from an atomic counter.
 //
 // Blocks.  A chunk is walked in blocks of 2^B steps.  The 2^B - 1 flips inside
-// a block are columns 0..B-1 in the ruler order of SCBS(B) (Sec. IV) and are
-// fully unrolled with compile-time column, row set and sign; only the flip at
-// a block boundary (column >= B) is chosen at run time, and it is uniform
-// across the warp.
+// a block are columns 0..B-1 in the ruler order of SCBS(B) (Sec. IV); in the
+// generated kernels they are fully unrolled with compile-time column, row set
+// and sign (the generic kernels roll them into a loop).  The flip at a block
+// boundary (column >= B) is chosen at run time, and it is uniform across the
+// warp.
 //
 // Product chain.  Rows are grouped by the first ordered column that touches
 // them: R_m.  A flip of column j changes only rows in R_0..R_j, so with
@@ -359,38 +360,6 @@ struct PairSteps {
     }
 };
 
-// Rolled form (policies with kRolled): the same 2^B steps as the paired
-// form, as a loop over groups of four steps with the column of the first
-// step chosen at run time.  A data-driven policy (the precompiled generic
-// kernels) gains nothing from unrolling and loses instruction-cache hits to
-// it.  Steps 4t+1 and 4t+3 flip column 0 (signs + and -), step 4t+2 flips
-// column 1 with sign bit 2 of 4t+2, i.e. t's low bit; step 4t (t > 0) flips
-// column ctz(4t) >= 2.  The policy's pair_terms<S>() adds the terms of two
-// steps that differ by a column-0 flip and applies that flip.  Levels 1..B-1
-// of the chain stay in registers (every Q index is a compile-time constant).
-template <class Pol, class A, int Bv>
-__device__ __forceinline__ void rolled_block(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
-                                             typename A::Blk &blk, int s_mid) {
-    static_assert(Bv >= 3, "the rolled block walks groups of four steps");
-#pragma unroll 1
-    for (int t = 0; t < (1 << (Bv - 2)); ++t) {
-        if (t != 0) {
-            const int l = t << 2;
-            const int j = __ffs(l) - 1;
-            const int s = (j == Bv - 1) ? s_mid : (((l >> (j + 1)) & 1) ? -1 : 1);
-            pol.flip_dyn(j, x, s);
-#pragma unroll
-            for (int M = Bv - 1; M >= 2; --M)
-                if (M <= j) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
-            Q[1] = pol.grp_dyn(1, x, Q[2]);
-        }
-        pol.template pair_terms<1>(x, Q[1], blk);
-        pol.flip_dyn(1, x, (t & 1) ? -1 : 1);
-        Q[1] = pol.grp_dyn(1, x, Q[2]);
-        pol.template pair_terms<-1>(x, Q[1], blk);
-    }
-}
-
 // ------------------------------------------------------------------ two-state chains
 // Policies with kDual never apply column 0 to x.  A step's product is
 //     prod_i x_i = (column 0 off) ? A_1 : B_1,
@@ -511,13 +480,9 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
         }
         P Q[Bv + 1];
         Q[Bv] = QB;
-        if constexpr (!Pol::kRolled) LevelsDown<Pol, A, Bv, Bv - 1>::run(pol, x, Q);
+        LevelsDown<Pol, A, Bv, Bv - 1>::run(pol, x, Q);
         typename A::Blk blk = A::blk_zero();
-        if constexpr (Pol::kRolled) {
-#pragma unroll
-            for (int M = Bv - 1; M >= 1; --M) Q[M] = pol.grp_dyn(M, x, Q[M + 1]);
-            rolled_block<Pol, A, Bv>(pol, x, Q, blk, s_mid);
-        } else if constexpr (Pol::kPaired) {
+        if constexpr (Pol::kPaired) {
             // steps 0 and 1 (column 0, sign +: bit 1 of 1 is 0), then pairs (2,3), (4,5), ...
             A::template blk_add<1>(blk, pol.template pair<1>(x, Q[1]));
             PairSteps<Pol, A, Bv, 2>::run(pol, x, Q, blk, s_mid);

@@ -1,12 +1,13 @@
 // generic_impl.cuh -- precompiled enumeration kernels (no per-matrix compilation).
 //
-// The walk of core.cuh with a matrix policy that reads the ordered matrix
-// from shared memory: a column flip or a group product runs over all NMAX
-// register slots with a warp-uniform predicate from the column's (group's)
-// bitmask, so every x index is a compile-time constant and x stays in
-// registers (the register-allocation condition of Sec. III-A) without knowing
-// the sparsity pattern at compile time.  The unrolled block is 2^B steps with
-// B = PERM_GENERIC_B.  Each generic_<arith>.cu file instantiates these
+// The Gray-code walk of core.cuh with a matrix policy that reads the ordered
+// matrix from a compact image in shared memory.  x stays in registers (the
+// register-allocation condition of Sec. III-A) without knowing the sparsity
+// pattern at compile time: every access to x goes through a switch whose
+// cases name x[k] with a compile-time k.  FP64 walks use the two-state chains
+// of core.cuh (walk_chunk_dual); exact walks (and FP64 at 48 slots) use one
+// chain with column 0 applied in pairs (walk_chunk_compact).  A block is 2^B
+// steps, B = PERM_GENERIC_B.  Each generic_<arith>.cu file instantiates these
 // templates for one arithmetic and every NMAX bucket; the build compiles the
 // files in parallel.
 #pragma once
@@ -68,12 +69,10 @@ template <int NMAX, class A>
 struct GenericPol {
     static constexpr int NX = NMAX;
     static constexpr int Bv = PERM_GENERIC_B;
-    static constexpr bool kPaired = false;
-    static constexpr bool kRolled = true;
     // Two-state chains (core.cuh) where a group's product can be shared by
     // both chains (FP64); ring products cannot, so the exact walks keep one
-    // chain and apply column 0 (pair_terms).  At 48 slots the second chain's
-    // registers would spill x, so that bucket keeps one chain too.
+    // chain and apply column 0 (walk_chunk_compact).  At 48 slots the second
+    // chain's registers would spill x, so that bucket keeps one chain too.
     static constexpr bool kDual = A::kProdIsX && NMAX <= 32;
     typedef typename A::X X;
     typedef typename A::P P;
@@ -204,8 +203,6 @@ struct GenericPol {
         }
         if (b < e) add_range(x, b, e, v, s);
     }
-    template <int J, int S>
-    __device__ __forceinline__ void flip(X (&x)[NX]) { flip_dyn(J, x, S); }
     template <int J>
     __device__ __forceinline__ void flip_rt(X (&x)[NX], int s) { flip_dyn(J, x, s); }
 
@@ -213,50 +210,19 @@ struct GenericPol {
         const int b = gbegin(g), e = gbegin(g + 1);
         return b < e ? prod_range(x, b, e, q) : q;
     }
-    template <int G>
-    __device__ __forceinline__ P grp(const X (&x)[NX], P q) const { return grp_dyn(G, x, q); }
 
-    // Steps l (even) and l+1 of a block, l+1 flipping column 0 with sign S:
-    // both terms share Q_1 and differ only in column 0's rows, the slots
-    // [0, |R_0|), whose values are the first |R_0| of the image.  One ladder
-    // multiplies the rows before the flip, applies it, and multiplies after.
-    template <int S>
-    __device__ __forceinline__ void pair_terms(X (&x)[NX], P q1, typename A::Blk &blk) {
+    // pair_terms with the column-0 sign S (+1 or -1) chosen at run time
+    __device__ __forceinline__ void pair_terms_rt(X (&x)[NX], P q1, typename A::Blk &blk, int S) {
+        const volatile V *v = m->val;
+        P p0 = q1, p1 = q1;
         if constexpr (FoldOf<A>::v) {
-            pair_terms_folded<S>(x, q1, blk);
-            return;
-        }
-        const volatile V *v = m->val;
-        P p0 = q1, p1 = q1;
-        switch (gbegin(1)) {
-#define PERM_PAIR_CASE(k)                                             \
-    case k + 1:                                                       \
-        if constexpr (k < NMAX) {                                     \
-            p0 = A::mul(p0, x[k]);                                    \
-            x[k] = A::template upd<S>(x[k], v[k]);                    \
-            p1 = A::mul(p1, x[k]);                                    \
-        }                                                             \
-        [[fallthrough]];
-            PERM_SLOT_CASES_DOWN(PERM_PAIR_CASE)
-#undef PERM_PAIR_CASE
-        default: break;
-        }
-        A::template blk_add<1>(blk, p0);
-        A::template blk_add<-1>(blk, p1);
-    }
-
-    // pair_terms with folded products (slot quadruples, as prod_range_folded)
-    template <int S>
-    __device__ __forceinline__ void pair_terms_folded(X (&x)[NX], P q1, typename A::Blk &blk) {
-        const volatile V *v = m->val;
-        P p0 = q1, p1 = q1;
-        int t0 = 1, t1 = 1;
-        switch (gbegin(1)) {
-#define PERM_FPAIR_CASE(k)                                            \
+            int t0 = 1, t1 = 1;
+            switch (gbegin(1)) {
+#define PERM_RFPAIR_CASE(k)                                           \
     case k + 1:                                                       \
         if constexpr (k < NMAX) {                                     \
             const X xo = x[k];                                        \
-            x[k] = A::template upd<S>(xo, v[k]);                      \
+            x[k] = A::upd_rt(xo, v[k], S);                            \
             if constexpr (k % 4 == 3) {                               \
                 t0 = xo;                                              \
                 t1 = x[k];                                            \
@@ -270,12 +236,38 @@ struct GenericPol {
             }                                                         \
         }                                                             \
         [[fallthrough]];
-            PERM_SLOT_CASES_DOWN(PERM_FPAIR_CASE)
-#undef PERM_FPAIR_CASE
-        default: break;
+                PERM_SLOT_CASES_DOWN(PERM_RFPAIR_CASE)
+#undef PERM_RFPAIR_CASE
+            default: break;
+            }
+        } else {
+            switch (gbegin(1)) {
+#define PERM_RPAIR_CASE(k)                                            \
+    case k + 1:                                                       \
+        if constexpr (k < NMAX) {                                     \
+            p0 = A::mul(p0, x[k]);                                    \
+            x[k] = A::upd_rt(x[k], v[k], S);                          \
+            p1 = A::mul(p1, x[k]);                                    \
+        }                                                             \
+        [[fallthrough]];
+                PERM_SLOT_CASES_DOWN(PERM_RPAIR_CASE)
+#undef PERM_RPAIR_CASE
+            default: break;
+            }
         }
         A::template blk_add<1>(blk, p0);
         A::template blk_add<-1>(blk, p1);
+    }
+    // levels from..to of the single chain (Qh, local memory), from >= to,
+    // each from the one above; returns level `to`
+    __device__ __forceinline__ P rebuild(const X (&x)[NX], int from, int to) {
+        P q = Qh[from + 1];
+#pragma unroll 1
+        for (int g = from; g >= to; --g) {
+            q = grp_dyn(g, x, q);
+            Qh[g] = q;
+        }
+        return q;
     }
 
     // qa *= x[k], qb *= x[k] + a_k0 for the rows k in [b, e) of column 0
@@ -352,27 +344,70 @@ struct GenericPol {
             flip_dyn(p, x, (int)((G >> p) & 1ull));
         }
     }
-    // all levels from the top group down to B
-    __device__ __forceinline__ P chain_init(const X (&x)[NX]) {
-        const int top = m->top;
-        P q = A::one();
-        for (int g = NMAX; g > top; --g) Qh[g] = q;
-        for (int g = top; g >= Bv; --g) {
-            q = grp_dyn(g, x, q);
-            Qh[g] = q;
-        }
-        return top >= Bv ? Qh[Bv] : q;
-    }
-    // after a flip of column j >= B: levels j..B
-    __device__ __forceinline__ P chain_hi(int j, const X (&x)[NX]) {
-        P q = Qh[j + 1];
-        for (int g = j; g >= Bv; --g) {
-            q = grp_dyn(g, x, q);
-            Qh[g] = q;
-        }
-        return q;
-    }
 };
+
+// The single-chain walk of the generic kernels (exact arithmetic, and FP64 at
+// 48 slots), arranged so that each data-driven piece of code -- a column
+// flip, a run of level rebuilds, the column-0 pair -- is inlined at one or two
+// places only: every chain level lives in one local array, the 2^(B-1) pairs
+// of a block are one rolled loop, and the column-0 sign is a run-time value.
+// (Slot ladders inlined at a dozen call sites made the exact kernels wait on
+// instruction fetch.)  Pair p of a block: the flip before it is column
+// 1 + ctz(p) with sign bit 1 + ctz(p) of p (Theorem 1; bit B of the block
+// start for column B-1), then steps 2p and 2p+1 differ by column 0 with sign
+// + for even p.
+template <int NMAX, class A>
+__device__ __forceinline__ typename A::Acc walk_chunk_compact(GenericPol<NMAX, A> &pol, u64 q, int K, int zero_skip,
+                                                              u64 &skipped) {
+    constexpr int Bv = PERM_GENERIC_B;
+    typedef typename A::X X;
+    typedef typename A::P P;
+    X x[NMAX];
+    const u64 g0 = q << K;
+    pol.init_x(x, g0 ^ (g0 >> 1));
+    const int top = pol.m->top;
+    for (int g = NMAX; g > top; --g) pol.Qh[g] = A::one();
+    typename A::Acc acc = A::acc_zero();
+    typename A::Blk mid = A::blk_zero();
+    const u64 nblocks = 1ull << (K - Bv);
+    for (u64 h = 0; h < nblocks; ++h) {
+        if (h != 0 && (h & 7) == 0) {
+            A::acc_merge(acc, mid);
+            mid = A::blk_zero();
+        }
+        const u64 gb = g0 + (h << Bv);
+        int from = top > Bv ? top : Bv;   // chunk start: every level down to B
+        if (h != 0) {
+            from = Bv + ctz64(h);
+            pol.flip_dyn(from, x, ((gb >> (from + 1)) & 1ull) ? -1 : 1);
+        }
+        const P qB = pol.rebuild(x, from, Bv);
+        const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
+        // the vote is also the warp's reconvergence point after the
+        // data-driven loops of the flips
+        const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(qB));
+        if (zero_skip && all_zero) {
+            pol.flip_dyn(Bv - 1, x, s_mid);   // the block's net effect on x
+            ++skipped;
+            continue;
+        }
+        typename A::Blk blk = A::blk_zero();
+#pragma unroll 1
+        for (int p = 0; p < (1 << (Bv - 1)); ++p) {
+            int lev = Bv - 1;
+            if (p != 0) {
+                lev = __ffs(p);   // 1 + ctz(p)
+                const int s = (lev == Bv - 1) ? s_mid : (((p >> lev) & 1) ? -1 : 1);
+                pol.flip_dyn(lev, x, s);
+            }
+            const P q1 = pol.rebuild(x, lev, 1);
+            pol.pair_terms_rt(x, q1, blk, (p & 1) ? -1 : 1);
+        }
+        A::blk_accumulate(mid, blk);
+    }
+    A::acc_merge(acc, mid);
+    return acc;
+}
 
 // The generic walk over any number of matrices (a single matrix is a batch
 // of one).  Warps of a persistent grid take 32-chunk tasks from one counter;
@@ -416,7 +451,11 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
         const bool live = q < bm.chunk_hi;
         if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
         GenericPol<NMAX, A> pol(slot);
-        typename A::Acc acc = walk_chunk<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
+        typename A::Acc acc;
+        if constexpr (GenericPol<NMAX, A>::kDual)
+            acc = walk_chunk_dual<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
+        else
+            acc = walk_chunk_compact<NMAX, A>(pol, q, bm.K, ba.zero_skip, skipped);
         if (!live) acc = A::acc_zero();
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
