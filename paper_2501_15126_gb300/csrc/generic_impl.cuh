@@ -464,8 +464,19 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
     if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
 }
 
+// Resident blocks the walk kernel is compiled for: exact rings of up to 96
+// bits at 32 slots, and up to 160 bits at 16, fit 80 registers without
+// spilling, so they run three blocks (24 warps) per SM; the rest two.
+template <class A> struct LimbsOf { static constexpr int v = 0; };
+template <int NL> struct LimbsOf<ArithExact<NL>> { static constexpr int v = NL; };
+template <int NL> struct LimbsOf<ArithExactFold<NL>> { static constexpr int v = NL; };
+template <int NMAX, class A> struct WalkMinBlocks {
+    static constexpr int L = LimbsOf<A>::v;
+    static constexpr int v = (L > 0 && ((NMAX == 16 && L <= 5) || (NMAX == 32 && L <= 3))) ? 3 : PERM_GENERIC_MIN_BLOCKS;
+};
+
 template <int NMAX, class A>
-__global__ void __launch_bounds__(256, PERM_GENERIC_MIN_BLOCKS) k_walk_generic(BatchArgs ba) {
+__global__ void __launch_bounds__(256, WalkMinBlocks<NMAX, A>::v) k_walk_generic(BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     generic_task_loop<NMAX, A>(ba, smem_raw + (size_t)warp * ba.slot_bytes);
