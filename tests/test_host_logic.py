@@ -184,3 +184,26 @@ def test_codegen_source_bakes_the_matrix():
     assert "perm_walk" in src and "x[0]" in src and "0x1." in src
     srck = A.codegen_source(a, reg_rows=6)
     assert "xg[" in srck
+
+
+def test_slot_layout_groups_and_column0_rows_by_next_column():
+    """Slots are sorted by group (first ordered column touching the row), and
+    group 0 (column 0's rows) by the next ordered column touching each row, so
+    every group and every set S_m of the two-state chains is a contiguous slot
+    range; column 0 touches exactly group 0."""
+    cases = [synth.single_er(24, 0.2, 1, values="01"), synth.band_plus(48, 3, 2, seed=3, values="f64"),
+             synth.single_er(28, 0.35, 7, values="f64"), synth.ones(9)]
+    for a in cases:
+        n = a.shape[0]
+        for ordering in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER, A.PERM_ORDER_NONE):
+            ins = A.inspect(a, ordering=ordering)
+            co, ro = list(ins.col_order[:n]), list(ins.row_order[:n])
+            grp = list(ins.group_of_row[:n])
+            assert grp == sorted(grp)
+            r0 = list(ins.group_size[:n])[0]
+            assert set(s for s in range(n) if a[ro[s], co[0]] != 0) == set(range(r0))
+            nxt = [next((p for p in range(1, n - 1) if a[ro[s], co[p]] != 0), n - 1) for s in range(r0)]
+            assert nxt == sorted(nxt), (ordering, nxt)
+            for s in range(n):   # the group is the first touching position
+                first = next((p for p in range(n) if a[ro[s], co[p]] != 0), n - 1)
+                assert grp[s] == first
