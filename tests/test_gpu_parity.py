@@ -311,3 +311,69 @@ def test_device_deadline_stops_a_long_walk_and_the_context_survives():
     res = A.batch([small, big], timeout_ms=50)
     assert res[1].status == A.PERM_ERR_TIMEOUT
     assert A.permanent(small, timeout_ms=60000).value == oracle.ryser_gray(small)
+
+
+# ------------------------------------------------------------------ closed forms on every path
+
+def _derangements(n):
+    d = [1, 0]
+    for k in range(2, n + 1):
+        d.append((k - 1) * (d[-1] + d[-2]))
+    return d[n]
+
+
+def _fib(k):
+    a, b = 0, 1
+    for _ in range(k):
+        a, b = b, a + b
+    return a
+
+
+def _closed_form_cases():
+    g = np.random.default_rng(77)
+    cases = [("J-I n=13", synth.ones_minus_identity(13), _derangements(13)),
+             ("J-I n=20", synth.ones_minus_identity(20), _derangements(20)),
+             ("tridiagonal n=30", synth.tridiagonal_ones(30), _fib(31))]
+    d = g.integers(1, 4, size=24)
+    p = synth.permutation_matrix(24, 5) * d[:, None]
+    cases.append(("scaled permutation n=24", p.astype(np.int64), int(np.prod(d))))
+    u = np.triu(g.integers(0, 3, size=(20, 20))).astype(np.int64)
+    np.fill_diagonal(u, g.integers(1, 4, size=20))
+    cases.append(("upper triangular n=20", u, int(np.prod(np.diag(u)))))
+    blocks = [synth.ones(6), synth.ones_minus_identity(7), synth.tridiagonal_ones(8)]
+    bd = np.zeros((21, 21), dtype=np.int64)
+    o = 0
+    for b in blocks:
+        bd[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    cases.append(("block diagonal n=21", bd, 720 * _derangements(7) * _fib(9)))
+    return cases
+
+
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN, "batch"])
+def test_closed_forms_exact_and_f64_on_every_path(engine):
+    """Closed forms on the generic and generated kernels and the batch launch,
+    in both arithmetics: D_n (J - I), Fibonacci (tridiagonal ones), a scaled
+    permutation, a triangular matrix and a block-diagonal product.  FP64 is
+    held to 1e-9 relative, or to 1e-12 of the sum of |terms| where the
+    alternating sum cancels beyond that (the triangular case: kappa 3.5e10)."""
+    cases = _closed_form_cases()
+    for name, a, want in cases:
+        af = a.astype(np.float64)
+        absum = float(oracle.nw_perm(af, threads=8)[1])
+        if engine == "batch":
+            r, rf = A.batch([a, af])
+        else:
+            r, rf = A.permanent(a, engine=engine), A.permanent(af, engine=engine)
+        assert r.value == want, (name, engine)
+        err = abs(rf.value - float(want))
+        assert err <= max(RTOL * abs(float(want)), 1e-12 * absum), (name, engine, rf.value, want)
+
+
+def test_cross_path_01_matrix_f64_equals_exact():
+    """A 0/1 matrix through the FP64 path agrees with the exact path within 1e-9."""
+    a = synth.single_er(24, 0.2, 1, values="01")
+    exact = A.permanent(a).value
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        f = A.permanent(a.astype(np.float64), engine=engine).value
+        assert rel_err(f, float(exact)) <= RTOL, (engine, f, exact)
