@@ -447,15 +447,15 @@ def run_profile_case(args):
     if args.profile_matrix == "batch28":
         # the largest class of the batch workload: its first n=28 matrix with these values
         a = next(it.a for it in synth.batch(count=400) if it.a.shape[0] == 28 and it.values == vals)
-    elif args.profile_exact:
-        a = synth.band_plus(48, 3, 2, seed=3, values="01")
+    elif args.profile_exact or args.profile_matrix == "band48":
+        a = synth.band_plus(48, 3, 2, seed=3, values=vals)
     else:
         a = workload_matrix()
     engine = A.PERM_ENGINE_GENERIC if args.profile_engine == "generic" else A.PERM_ENGINE_CODEGEN
     n = a.shape[0]
     # a prefix of the walk, or (when it covers the range) the whole walk with its own ring width
     g_hi = 0 if args.profile_log2 >= n - 1 else 1 << args.profile_log2
-    p = A.Plan(a, g_lo=0, g_hi=g_hi, engine=engine)
+    p = A.Plan(a, g_lo=0, g_hi=g_hi, engine=engine, flags=A.PERM_FLAG_PAIRED_CHAIN if args.profile_paired else 0)
     for _ in range(args.steps):
         r = p.compute()
     print(json.dumps({"profile_case": vals, "matrix": args.profile_matrix, "n": n, "engine": args.profile_engine,
@@ -478,9 +478,11 @@ def main():
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
     ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
-    ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28"],
+    ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28", "band48"],
                     help="bench: the n=36 bench matrix (the n=48 band with --profile-exact); "
-                         "batch28: an n=28 matrix of the batch workload")
+                         "batch28: an n=28 matrix of the batch workload; band48: the n=48 band-plus-off-band matrix")
+    ap.add_argument("--profile-paired", action="store_true",
+                    help="generated FP64 kernels: the paired chain even where two-state chains are cheaper")
     ap.add_argument("--batch-count", type=int, default=10_000)
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--duration", type=float, default=60.0)

@@ -100,7 +100,9 @@ enum {
 /* Option flags. */
 enum {
     PERM_FLAG_NO_KERNEL_CACHE = 1,  /* codegen: compile even if this source was compiled before */
-    PERM_FLAG_NO_GRAPH = 2          /* perm_compute: never replay the plan as a CUDA graph     */
+    PERM_FLAG_NO_GRAPH = 2,         /* perm_compute: never replay the plan as a CUDA graph     */
+    PERM_FLAG_PAIRED_CHAIN = 4      /* codegen FP64: the paired chain even where the two-state */
+                                    /*   chains cost fewer operations per step                 */
 };
 
 /* Options; a zeroed struct (or NULL) means "choose automatically". */

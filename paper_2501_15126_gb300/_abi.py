@@ -23,6 +23,7 @@ PERM_ORDER_AUTO, PERM_ORDER_NONE, PERM_ORDER_DEGREE, PERM_ORDER_PAPER = 0, 1, 2,
 PERM_ENGINE_AUTO, PERM_ENGINE_GENERIC, PERM_ENGINE_CODEGEN = 0, 1, 2
 PERM_FLAG_NO_KERNEL_CACHE = 1
 PERM_FLAG_NO_GRAPH = 2
+PERM_FLAG_PAIRED_CHAIN = 4
 
 c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 

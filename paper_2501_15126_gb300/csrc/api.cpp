@@ -265,6 +265,26 @@ void normalise_split(const Layout &L, int *k, int *c) {
     if (*k < 1) *k = 1;
 }
 
+// The generated kernel's layout: the Algorithm 4 split (or the caller's
+// register rows) and, for FP64, the cheaper of the paired chain and the
+// two-state chains under the cost model.
+static void codegen_layout(perm_plan_s &P) {
+    const int n = P.m.n;
+    int k = n, c = n - 1;
+    const double gr = P.opts.gr_ratio > 0 ? P.opts.gr_ratio : kDefaultGRRatio;
+    partition_alg4(P.L, gr, kCodegenBaseRegs, &k, &c);   // Algorithm 4
+    if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
+    normalise_split(P.L, &k, &c);
+    P.k = k;
+    P.c = c;
+    P.dual = false;
+    if (P.arith == 0) {
+        const double paired = cost_per_step_paired(P.L), dual = cost_per_step_dual(P.L, true);
+        P.dual = dual < paired && !(P.opts.flags & PERM_FLAG_PAIRED_CHAIN);
+        P.ops_per_step = P.dual ? dual : paired;
+    }
+}
+
 perm_status_t plan_device_setup(perm_plan_s &P) {
     const int n = P.m.n;
     cudaError_t e;
@@ -306,14 +326,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
             if (st != PERM_OK) return st;
         }
     } else {
-        int k = n, c = n - 1;
-        const double gr = P.opts.gr_ratio > 0 ? P.opts.gr_ratio : kDefaultGRRatio;
-        partition_alg4(P.L, gr, kCodegenBaseRegs, &k, &c);   // Algorithm 4
-        if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
-        normalise_split(P.L, &k, &c);
-        P.k = k;
-        P.c = c;
-        if (P.arith == 0) P.ops_per_step = cost_per_step_paired(P.L);
+        codegen_layout(P);
         std::string err;
         perm_status_t st = codegen_build(P, err);
         if (st != PERM_OK) return fail(st, err);
@@ -616,13 +629,7 @@ perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opt
     perm_plan_s P;
     perm_status_t st = plan_prepare(A, opts, P);
     if (st != PERM_OK) return st;
-    const int n = P.m.n;
-    int k = n, c = n - 1;
-    partition_alg4(P.L, (opts && opts->gr_ratio > 0) ? opts->gr_ratio : kDefaultGRRatio, kCodegenBaseRegs, &k, &c);
-    if (opts && opts->reg_rows > 0) split_for_rows(P.L, opts->reg_rows, &k, &c);
-    normalise_split(P.L, &k, &c);
-    P.k = k;
-    P.c = c;
+    codegen_layout(P);
     std::string src = codegen_source(P);
     if (len) *len = (int64_t)src.size();
     if (buf && cap > 0) {

@@ -150,6 +150,80 @@ struct Emitter {
         for (int s = P.L.group_begin[g]; s < P.L.group_begin[g + 1]; ++s)
             o << ind << "q = A::mul(q, " << slot(s) << ");\n";
     }
+    // two-state chains: level g holds group g and S_g (column 0's rows next
+    // touched by column g)
+    bool level_nonempty(int g) const {
+        return P.L.group_begin[g + 1] > P.L.group_begin[g] || P.L.s_begin[g + 1] > P.L.s_begin[g];
+    }
+    std::vector<int> high_levels2(int B) const {
+        std::vector<int> v;
+        for (int g = n - 1; g >= B; --g)
+            if (level_nonempty(g)) v.push_back(g);
+        return v;
+    }
+    // qa = ain * prod_{group g} x * prod_{S_g} x, qb = bin * prod_{group g} x * prod_{S_g} (x + a_0)
+    void level2_code(int g, const std::string &ain, const std::string &bin, const char *ind) {
+        const int b = P.L.group_begin[g], e = P.L.group_begin[g + 1];
+        if (b < e) {
+            o << ind << "{\n" << ind << "    P t = " << slot(b) << ";\n";
+            for (int s = b + 1; s < e; ++s) o << ind << "    t = t * " << slot(s) << ";\n";
+            o << ind << "    qa = " << ain << " * t;\n" << ind << "    qb = " << bin << " * t;\n" << ind << "}\n";
+        } else if (ain != "qa") {
+            o << ind << "qa = " << ain << ";\n" << ind << "qb = " << bin << ";\n";
+        }
+        for (int s = P.L.s_begin[g]; s < P.L.s_begin[g + 1]; ++s) {
+            o << ind << "qa = qa * " << slot(s) << ";\n";
+            o << ind << "qb = qb * (" << slot(s) << " + " << lit(P, value(0, s)) << ");\n";
+        }
+    }
+    // the level functions, start and rebuild of the two-state chains
+    void emit_dual(int B) {
+        const std::vector<int> hi2 = high_levels2(B);
+        o << "    template <int M> __device__ __forceinline__ void level2c(const X (&x)[NX], P qa_in, P qb_in, P &qa, P &qb) const {\n";
+        for (int g = 1; g < B; ++g) {
+            o << "        " << (g > 1 ? "else " : "") << "if constexpr (M == " << g << ") {\n";
+            if (g < n) level2_code(g, "qa_in", "qb_in", "            ");
+            else o << "            qa = qa_in;\n            qb = qb_in;\n";
+            o << "        }\n";
+        }
+        o << "    }\n";
+        o << "    __device__ __forceinline__ void level2(int M, const X (&x)[NX], P qa_in, P qb_in, P &qa, P &qb) const {\n";
+        o << "        switch (M) {\n";
+        for (int g = 1; g < B; ++g) o << "        case " << g << ": level2c<" << g << ">(x, qa_in, qb_in, qa, qb); break;\n";
+        o << "        default: qa = qa_in; qb = qb_in; break;\n        }\n    }\n";
+        o << "    __device__ __forceinline__ void chain_init2(const X (&x)[NX], P &QA, P &QB) {\n";
+        o << "        P qa = A::one(), qb = A::one();\n";
+        for (int g : hi2) {
+            level2_code(g, "qa", "qb", "        ");
+            o << "        QA" << g << " = qa;\n        QB" << g << " = qb;\n";
+        }
+        o << "        QA = qa;\n        QB = qb;\n    }\n";
+        auto above2 = [&](int g) -> int {
+            for (int h = g + 1; h < n; ++h)
+                if (h >= B && level_nonempty(h)) return h;
+            return -1;
+        };
+        o << "    __device__ __forceinline__ void chain_hi2(int j, const X (&x)[NX], P &QA, P &QB) {\n";
+        o << "        P qa, qb;\n        switch (j) {\n";
+        for (int j = B; j < n - 1; ++j) {
+            const int a = above2(j);
+            if (a >= 0) o << "        case " << j << ": qa = QA" << a << "; qb = QB" << a << "; break;\n";
+            else o << "        case " << j << ": qa = A::one(); qb = A::one(); break;\n";
+        }
+        o << "        default: qa = A::one(); qb = A::one(); break;\n        }\n";
+        o << "        switch (j) {\n";
+        for (int j = n - 2; j >= B; --j) {
+            o << "        case " << j << ":\n";
+            if (level_nonempty(j)) {
+                level2_code(j, "qa", "qb", "            ");
+                o << "            QA" << j << " = qa;\n            QB" << j << " = qb;\n";
+            }
+            o << "            [[fallthrough]];\n";
+        }
+        o << "        default: break;\n        }\n";
+        o << "        QA = qa;\n        QB = qb;\n    }\n";
+    }
+
     // nonempty chain levels >= B, descending
     std::vector<int> high_levels(int B) const {
         std::vector<int> v;
@@ -169,10 +243,15 @@ struct Emitter {
         o << "struct GenPol {\n";
         o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
         o << "    static constexpr bool kPaired = " << (P.arith == 0 ? "true" : "false") << ";\n";
-        o << "    static constexpr bool kDual = false;\n";
+        o << "    static constexpr bool kDual = " << (P.dual ? "true" : "false") << ";\n";
+        o << "    static constexpr bool kUnrolledDual = true;\n";
         o << "    typedef A::X X;\n    typedef A::P P;\n";
         o << "    X *xg;\n    unsigned long long stride;\n";
-        for (int g : hi) o << "    P Q" << g << ";\n";
+        if (P.dual) {
+            for (int g : high_levels2(B)) o << "    P QA" << g << ", QB" << g << ";\n";
+        } else {
+            for (int g : hi) o << "    P Q" << g << ";\n";
+        }
         // flips inside the unrolled block (static column, static or runtime sign)
         o << "    template <int J, int S> __device__ __forceinline__ void flip(X (&x)[NX]) {\n";
         for (int p = 0; p < B && p < n - 1; ++p) {
@@ -257,6 +336,12 @@ struct Emitter {
         o << "        unsigned long long U = warp_or64(G);\n";
         o << "        while (U) {\n            const int p = ctz64(U);\n            U &= U - 1;\n";
         o << "            flip_dyn(p, x, (int)((G >> p) & 1ull));\n        }\n    }\n";
+        if (P.dual) {
+            emit_dual(B);
+            o << "};\n}  // namespace pk\n\n";
+            emit_kernel(B);
+            return o.str();
+        }
         // high chain levels
         auto above = [&](int g) -> std::string {   // the nonempty level just above g
             for (int h = g + 1; h < n; ++h)
@@ -290,6 +375,10 @@ struct Emitter {
         o << "        default: break;\n        }\n";
         o << "        return q;\n    }\n";
         o << "};\n}  // namespace pk\n\n";
+        emit_kernel(B);
+        return o.str();
+    }
+    void emit_kernel(int B) {
         o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock << ", " << min_blocks
           << ") perm_walk(pk::WalkArgs wa, void *xg_base) {\n";
         o << "    pk::GenPol pol;\n";
@@ -297,7 +386,6 @@ struct Emitter {
         o << "    pol.stride = (unsigned long long)gridDim.x * blockDim.x;\n";
         o << "    pol.xg = reinterpret_cast<pk::GenPol::X *>(xg_base) + tid;\n";
         o << "    pk::walk_tasks<pk::GenPol, pk::A, " << B << ">(pol, wa);\n}\n";
-        return o.str();
     }
 };
 

@@ -395,6 +395,40 @@ __device__ __forceinline__ void dual_block(Pol &pol, typename A::X (&x)[Pol::NX]
     }
 }
 
+// The same block unrolled (generated kernels): pair P's flip has a
+// compile-time column and sign, and level2c<M> compile-time rows.
+template <class Pol, class A, int Bv, int M>
+struct LevelsDown2 {
+    static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&QA)[Bv + 1],
+                                               typename A::P (&QB)[Bv + 1]) {
+        if constexpr (M >= 1) {
+            pol.template level2c<M>(x, QA[M + 1], QB[M + 1], QA[M], QB[M]);
+            LevelsDown2<Pol, A, Bv, M - 1>::run(pol, x, QA, QB);
+        }
+    }
+};
+
+template <class Pol, class A, int Bv, int Pp>
+struct DualSteps {
+    static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&QA)[Bv + 1],
+                                               typename A::P (&QB)[Bv + 1], typename A::Blk &blk, int s_mid) {
+        if constexpr (Pp < (1 << (Bv - 1))) {
+            if constexpr (Pp > 0) {
+                constexpr int J = 1 + Ctz<Pp>::v;
+                if constexpr (J == Bv - 1) {
+                    pol.template flip_rt<J>(x, s_mid);
+                } else {
+                    constexpr int S = ((Pp >> J) & 1) ? -1 : 1;
+                    pol.template flip<J, S>(x);
+                }
+                LevelsDown2<Pol, A, Bv, J>::run(pol, x, QA, QB);
+            }
+            A::template blk_add<(Pp & 1) ? -1 : 1>(blk, A::diff(QA[1], QB[1]));
+            DualSteps<Pol, A, Bv, Pp + 1>::run(pol, x, QA, QB, blk, s_mid);
+        }
+    }
+};
+
 template <class Pol, class A, int Bv>
 __device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int K, int zero_skip, u64 &skipped) {
     typedef typename A::X X;
@@ -433,7 +467,8 @@ __device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int 
 #pragma unroll
         for (int M = Bv - 1; M >= 1; --M) pol.level2(M, x, LA[M + 1], LB[M + 1], LA[M], LB[M]);
         typename A::Blk blk = A::blk_zero();
-        dual_block<Pol, A, Bv>(pol, x, LA, LB, blk, s_mid);
+        if constexpr (Pol::kUnrolledDual) DualSteps<Pol, A, Bv, 0>::run(pol, x, LA, LB, blk, s_mid);
+        else dual_block<Pol, A, Bv>(pol, x, LA, LB, blk, s_mid);
         A::blk_accumulate(mid, blk);
     }
     A::acc_merge(acc, mid);

@@ -74,6 +74,7 @@ struct GenericPol {
     // chain and apply column 0 (walk_chunk_compact).  At 48 slots the second
     // chain's registers would spill x, so that bucket keeps one chain too.
     static constexpr bool kDual = A::kProdIsX && NMAX <= 32;
+    static constexpr bool kUnrolledDual = false;   // the pairs of a block are a rolled loop
     typedef typename A::X X;
     typedef typename A::P P;
     typedef typename A::V V;

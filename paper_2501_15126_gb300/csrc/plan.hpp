@@ -18,6 +18,7 @@ struct perm_plan_s {
     int arith = 0;            // 0 = FP64, 1..3 = exact, results stored as `arith` 64-bit words
     int limbs = 0;            // 0 = FP64, else the walk's ring Z/2^(32 limbs): 2 arith - 1 or 2 arith
     bool fold = false;        // exact: every row's absolute sum <= 127 (folded products)
+    bool dual = false;        // generated FP64 kernel with two-state chains (cheaper than pairing)
     int kind() const { return 2 * limbs + (fold ? 1 : 0); }   // generic kernel family
     uint64_t total = 0;       // 2^(n-1)
     uint64_t g_lo = 0, g_hi = 0;

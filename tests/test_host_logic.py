@@ -207,3 +207,17 @@ def test_slot_layout_groups_and_column0_rows_by_next_column():
             for s in range(n):   # the group is the first touching position
                 first = next((p for p in range(n) if a[ro[s], co[p]] != 0), n - 1)
                 assert grp[s] == first
+
+
+def test_generated_fp64_kernel_picks_the_cheaper_chain():
+    """Generated FP64 kernels use two-state chains where the cost model says
+    they take fewer operations per step than the paired chain (the n=48 band:
+    column 0's rows are next touched late), and the paired chain otherwise (the
+    n=36 workload); PERM_FLAG_PAIRED_CHAIN forces the paired chain."""
+    band = synth.band_plus(48, 3, 2, seed=3, values="f64")
+    cfg2 = synth.single_er(36, 0.15, 2, values="f64")
+    assert "kDual = true" in A.codegen_source(band)
+    assert "kDual = false" in A.codegen_source(band, flags=A.PERM_FLAG_PAIRED_CHAIN)
+    assert "kDual = false" in A.codegen_source(cfg2)
+    assert "kDual = false" in A.codegen_source(synth.band_plus(48, 3, 2, seed=3, values="01"))   # exact: one chain
+
