@@ -16,6 +16,7 @@
 // driver API; kernels are cached by their source text for the life of the
 // process.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -146,9 +147,36 @@ struct Emitter {
         for (int s = 0; s < n; ++s)
             if (has(p, s)) update(p, s, mode, ind);
     }
+    // q *= the rows of group g.  Exact walks multiply runs of rows in 32 bits
+    // first while the product of the rows' absolute sums (which bound |x_i|
+    // at every Gray index) stays below 2^31, then fold each run into the ring
+    // with one multiplication.
     void group_product(int g, const char *ind) {
-        for (int s = P.L.group_begin[g]; s < P.L.group_begin[g + 1]; ++s)
-            o << ind << "q = A::mul(q, " << slot(s) << ");\n";
+        const int b = P.L.group_begin[g], e = P.L.group_begin[g + 1];
+        if (P.arith == 0) {
+            for (int s = b; s < e; ++s) o << ind << "q = A::mul(q, " << slot(s) << ");\n";
+            return;
+        }
+        int s = b;
+        while (s < e) {
+            double bound = row_abs_sum(s);
+            int t = s + 1;
+            while (t < e && bound * row_abs_sum(t) < 2147483647.0) bound *= row_abs_sum(t++);
+            if (t == s + 1) {
+                o << ind << "q = A::mul(q, " << slot(s) << ");\n";
+            } else {
+                o << ind << "q = A::mul(q, " << slot(s);
+                for (int u = s + 1; u < t; ++u) o << " * " << slot(u);
+                o << ");\n";
+            }
+            s = t;
+        }
+    }
+    double row_abs_sum(int s) const {
+        const int r = P.L.row_order[s];
+        double a = 0.0;
+        for (int j = 0; j < n; ++j) a += std::fabs(P.m.fval(r, j));
+        return std::max(a, 1.0);
     }
     // two-state chains: level g holds group g and S_g (column 0's rows next
     // touched by column g)

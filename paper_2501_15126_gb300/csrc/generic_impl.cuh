@@ -212,7 +212,11 @@ struct GenericPol {
         return b < e ? prod_range(x, b, e, q) : q;
     }
 
-    // pair_terms with the column-0 sign S (+1 or -1) chosen at run time
+    // Steps l (even) and l+1 of a block, l+1 flipping column 0 with sign S
+    // (+1 or -1, run time): both terms share Q_1 and differ only in column
+    // 0's rows, the slots [0, |R_0|), whose values are the image's first
+    // |R_0|.  One ladder multiplies the rows before the flip, applies it, and
+    // multiplies after.
     __device__ __forceinline__ void pair_terms_rt(X (&x)[NX], P q1, typename A::Blk &blk, int S) {
         const volatile V *v = m->val;
         P p0 = q1, p1 = q1;
