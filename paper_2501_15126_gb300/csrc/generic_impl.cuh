@@ -21,8 +21,9 @@
 #define PERM_GENERIC_B 5
 #endif
 
-// Resident 256-thread blocks per SM the kernels are compiled for (their
-// register budget): 2 -> 128 registers, 3 -> 80.
+// Resident 256-thread blocks per SM the walk kernels are compiled for by
+// default (their register budget): 2 -> 128 registers, 3 -> 80.  Narrow exact
+// rings take three (WalkMinBlocks below).
 #ifndef PERM_GENERIC_MIN_BLOCKS
 #define PERM_GENERIC_MIN_BLOCKS 2
 #endif
