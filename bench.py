@@ -115,7 +115,8 @@ def traffic_record(kernel_hash: str):
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for name in ("core.cuh", "codegen.cpp", "devmat.h"):
+    # the walk code, the generator, and the host code that picks layout and scheme
+    for name in ("core.cuh", "codegen.cpp", "devmat.h", "host.cpp", "api.cpp"):
         h.update(open(os.path.join(ROOT, "paper_2501_15126_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 

@@ -265,7 +265,9 @@ double cost_per_step_dual(const Layout &L, bool shared_product) {
         rate += w;                                             // level m is rebuilt by any column >= m
         const int r = L.group_begin[m + 1] - L.group_begin[m];
         const int sm = L.s_begin[m + 1] - L.s_begin[m];
-        const double level = (shared_product ? (r ? r + 2.0 : 0.0) : 2.0 * r) + 3.0 * sm;
+        // shared: the group's product (r - 1 multiplications) into both chains (2);
+        // S_m rows: x and x + a_0 into the two chains (3 operations per row)
+        const double level = (shared_product ? (r ? r + 1.0 : 0.0) : 2.0 * r) + 3.0 * sm;
         total += rate * level;
     }
     const double w0 = std::ldexp(1.0, n - 2) / steps;         // pairs of steps
