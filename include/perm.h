@@ -84,10 +84,15 @@ typedef struct {
 /* Column ordering (Sec. V and Sec. VI-B).  The last column of the order is the
    one the Nijenhuis-Wilf variant never flips. */
 enum {
-    PERM_ORDER_AUTO = 0,    /* the cheaper of DEGREE and PAPER under the step-cost model */
+    PERM_ORDER_AUTO = 0,    /* the cheaper of DEGREE and PAPER under the step-cost model, */
+                            /*   then SEARCH from it                                      */
     PERM_ORDER_NONE = 1,    /* columns as given                                          */
     PERM_ORDER_DEGREE = 2,  /* ascending nonzero count (Sec. VI-B, CPU-SparsePerman)    */
-    PERM_ORDER_PAPER = 3    /* PermanentOrdering, Algorithm 3                            */
+    PERM_ORDER_PAPER = 3,   /* PermanentOrdering, Algorithm 3                            */
+    PERM_ORDER_SEARCH = 4   /* reported when AUTO's pairwise column swaps lowered the     */
+                            /*   cost model of the scheme the walk runs (FP64: two-state */
+                            /*   or paired chain; exact: one chain); as an option, same  */
+                            /*   as AUTO                                                  */
 };
 
 /* Which kernel family runs the walk. */
@@ -282,6 +287,8 @@ typedef struct {
     double ops_per_step_paper;   /* the same walk with a full product per step       */
     int32_t exact_limbs;         /* 32-bit limbs of the whole walk's ring: 2w-1 or 2w */
     int32_t reserved0;
+    double ops_per_step_walk;    /* cost model of the scheme the walk runs (FP64:     */
+                                 /*   two-state or paired chain; exact: one chain)    */
 } perm_inspect_t;
 
 perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts, perm_inspect_t *out);

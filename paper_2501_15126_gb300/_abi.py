@@ -19,7 +19,7 @@ PERM_OK, PERM_ERR_ARG, PERM_ERR_SIZE, PERM_ERR_PATTERN, PERM_ERR_OVERFLOW, PERM_
     PERM_ERR_NOMEM, PERM_ERR_TIMEOUT, PERM_ERR_BUSY, PERM_ERR_NOT_READY, PERM_ERR_CANCELLED, PERM_ERR_INTERNAL = range(13)
 PERM_F64, PERM_I64 = 0, 1
 PERM_CSR, PERM_CSC = 0, 1
-PERM_ORDER_AUTO, PERM_ORDER_NONE, PERM_ORDER_DEGREE, PERM_ORDER_PAPER = 0, 1, 2, 3
+PERM_ORDER_AUTO, PERM_ORDER_NONE, PERM_ORDER_DEGREE, PERM_ORDER_PAPER, PERM_ORDER_SEARCH = 0, 1, 2, 3, 4
 PERM_ENGINE_AUTO, PERM_ENGINE_GENERIC, PERM_ENGINE_CODEGEN = 0, 1, 2
 PERM_FLAG_NO_KERNEL_CACHE = 1
 PERM_FLAG_NO_GRAPH = 2
@@ -67,7 +67,8 @@ class Inspect(ctypes.Structure):
                 ("col_order", c_i32 * 64), ("row_order", c_i32 * 64), ("group_of_row", c_i32 * 64),
                 ("group_size", c_i32 * 64), ("col_nnz", c_i32 * 64), ("reg_rows", c_i32), ("reg_cols", c_i32),
                 ("exact_words", c_i32), ("bound_log2", c_dbl), ("ops_per_step", c_dbl),
-                ("ops_per_step_paper", c_dbl), ("exact_limbs", c_i32), ("reserved0", c_i32)]
+                ("ops_per_step_paper", c_dbl), ("exact_limbs", c_i32), ("reserved0", c_i32),
+                ("ops_per_step_walk", c_dbl)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -167,7 +167,8 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     if (P.g_lo > P.g_hi || P.g_hi > P.total) return fail(PERM_ERR_ARG, "sub-range outside [0, 2^(n-1))");
     if (P.subrange && ((P.g_lo % 32) || ((P.g_hi % 32) && P.g_hi != P.total)))
         return fail(PERM_ERR_ARG, "sub-range ends must be multiples of 32");
-    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_PAPER) return fail(PERM_ERR_ARG, "bad ordering");
+    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_SEARCH) return fail(PERM_ERR_ARG, "bad ordering");
+    if (opts.ordering == PERM_ORDER_SEARCH) opts.ordering = PERM_ORDER_AUTO;
     if (opts.engine < 0 || opts.engine > PERM_ENGINE_CODEGEN) return fail(PERM_ERR_ARG, "bad engine");
     if (opts.exact_words < 0 || opts.exact_words > 3) return fail(PERM_ERR_ARG, "exact_words must be 0..3");
     if (opts.chunk_log2 < 0 || opts.chunk_log2 > 63) return fail(PERM_ERR_ARG, "bad chunk_log2");
@@ -580,7 +581,8 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     const char *err = nullptr;
     perm_status_t st = ingest(A, m, &err);
     if (st != PERM_OK) return fail(st, err);
-    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_PAPER) return fail(PERM_ERR_ARG, "bad ordering");
+    if (opts.ordering < 0 || opts.ordering > PERM_ORDER_SEARCH) return fail(PERM_ERR_ARG, "bad ordering");
+    if (opts.ordering == PERM_ORDER_SEARCH) opts.ordering = PERM_ORDER_AUTO;
     const Layout L = choose_layout(m, opts.ordering);
     out->n = m.n;
     out->structurally_zero = has_perfect_matching(m) ? 0 : 1;
@@ -599,6 +601,7 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     out->bound_log2 = bound_log2(m);
     out->exact_words = m.is_int ? exact_words_for(out->bound_log2, m.n) : 0;
     out->exact_limbs = out->exact_words ? exact_limbs_for(out->bound_log2, m.n) : 0;
+    out->ops_per_step_walk = walk_cost_per_step(L, !m.is_int);
     out->ops_per_step = cost_per_step(L, false);
     out->ops_per_step_paper = cost_per_step(L, true);
     return PERM_OK;

@@ -274,6 +274,85 @@ double cost_per_step_dual(const Layout &L, bool shared_product) {
     return total + w0 * 2.0;
 }
 
+// The step-cost model of the scheme a plan will run, straight from a column
+// order (group sizes, column-0 rows by next column, column sizes: O(n) with
+// bit masks), for the order search below.  Same formulas as cost_per_step
+// (exact: one chain), cost_per_step_paired and cost_per_step_dual (FP64:
+// the cheaper of the two for long walks, two-state chains for short ones).
+static double order_cost(const Matrix &m, const int *cols, bool fp64, bool long_walk) {
+    const int n = m.n;
+    int R[kNMax], d[kNMax], S[kNMax + 1] = {};
+    uint64_t seen = 0, r0 = 0;
+    for (int p = 0; p < n; ++p) {
+        const uint64_t cm = m.colmask[cols[p]];
+        d[p] = __builtin_popcountll(cm);
+        const uint64_t nw = cm & ~seen;
+        R[p] = __builtin_popcountll(nw);
+        seen |= cm;
+        if (p == 0) r0 = nw;
+    }
+    uint64_t rem = r0;
+    for (int p = 1; p < n - 1; ++p) {
+        const uint64_t hit = m.colmask[cols[p]] & rem;
+        S[p] = __builtin_popcountll(hit);
+        rem &= ~hit;
+    }
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    if (!fp64) {   // one chain, column 0 applied (cost_per_step)
+        double total = 0.0, prefix = 0.0;
+        for (int j = 0; j <= n - 2; ++j) {
+            prefix += R[j];
+            total += std::ldexp(1.0, n - j - 2) / steps * (d[j] + prefix + 1.0);
+        }
+        return total;
+    }
+    const double w0 = std::ldexp(1.0, n - 2) / steps;
+    double dual = 0.0, rate = 0.0;
+    for (int j = n - 2; j >= 1; --j) {
+        const double w = std::ldexp(1.0, n - j - 2) / steps;
+        dual += w * d[j];
+        rate += w;
+        dual += rate * ((R[j] ? R[j] + 1.0 : 0.0) + 3.0 * S[j]);
+    }
+    dual += 2.0 * w0;
+    if (!long_walk) return dual;
+    double paired = 0.0, prefix = 0.0;
+    for (int j = 1; j <= n - 2; ++j) {
+        prefix += R[j];
+        paired += std::ldexp(1.0, n - j - 2) / steps * (d[j] + prefix);
+    }
+    paired += w0 * (R[0] == 1 ? 2.0 : 3.0 * R[0] - 1.0);
+    return std::min(dual, paired);
+}
+
+// Pairwise column swaps, first improvement, until none lowers the cost model
+// (at most 16 sweeps).
+static void search_order(const Matrix &m, int *cols, bool fp64, bool long_walk) {
+    const int n = m.n;
+    double best = order_cost(m, cols, fp64, long_walk);
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        bool improved = false;
+        for (int i = 0; i + 1 < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                std::swap(cols[i], cols[j]);
+                const double c = order_cost(m, cols, fp64, long_walk);
+                if (c < best - 1e-12) {
+                    best = c;
+                    improved = true;
+                } else {
+                    std::swap(cols[i], cols[j]);
+                }
+            }
+        if (!improved) break;
+    }
+}
+
+double walk_cost_per_step(const Layout &L, bool fp64) {
+    if (!fp64) return cost_per_step(L, false);
+    const double dual = cost_per_step_dual(L, true);
+    return L.n >= 31 ? std::min(dual, cost_per_step_paired(L)) : dual;
+}
+
 Layout choose_layout(const Matrix &m, int ordering_opt) {
     int cols[kNMax], rows[kNMax];
     if (ordering_opt == PERM_ORDER_NONE) { order_none(m, cols); return make_layout(m, cols, PERM_ORDER_NONE); }
@@ -283,7 +362,18 @@ Layout choose_layout(const Matrix &m, int ordering_opt) {
     if (ordering_opt == PERM_ORDER_PAPER) return paper;
     order_degree(m, cols);
     Layout deg = make_layout(m, cols, PERM_ORDER_DEGREE);
-    return cost_per_step(deg, false) < cost_per_step(paper, false) ? deg : paper;
+    Layout start = cost_per_step(deg, false) < cost_per_step(paper, false) ? deg : paper;
+    // AUTO / SEARCH: for walks of 2^30 steps and more (the generated kernels'
+    // range), refine the better order under the model of the scheme the walk
+    // will run.  The search takes about 0.2 ms of host time at n = 28, more
+    // than shorter walks would gain.
+    if (m.n < 31) return start;
+    for (int p = 0; p < m.n; ++p) cols[p] = start.col_order[p];
+    const bool fp64 = !m.is_int, long_walk = true;
+    const double before = order_cost(m, cols, fp64, long_walk);
+    search_order(m, cols, fp64, long_walk);
+    if (!(order_cost(m, cols, fp64, long_walk) < before - 1e-12)) return start;
+    return make_layout(m, cols, PERM_ORDER_SEARCH);
 }
 
 int64_t threads_for_regs(int regs) {

@@ -107,6 +107,10 @@ int exact_words_for(double bound, int n);
 // folded into a second chain): flips of columns >= 1, the levels they
 // rebuild, and one difference and accumulation per pair of steps.
 double cost_per_step_dual(const Layout &L, bool shared_product);
+// The model of the scheme a walk of this layout runs: FP64 two-state chains
+// (or, for walks long enough for the generated kernels, the cheaper of those
+// and the paired chain); exact: one chain.
+double walk_cost_per_step(const Layout &L, bool fp64);
 // The fewest 32-bit limbs (2..6) of a ring that holds 2^(n-1) perm with sign
 // and margin, or 0.
 int exact_limbs_for(double bound, int n);

@@ -122,7 +122,11 @@ def test_orderings_and_cost_model():
     auto = A.inspect(a)
     nnz = [int((a[:, j] != 0).sum()) for j in range(36)]
     assert [nnz[c] for c in list(deg.col_order)[:36]] == sorted(nnz)
-    assert auto.ops_per_step == min(deg.ops_per_step, pap.ops_per_step)
+    # AUTO starts from the cheaper of DEGREE and PAPER and searches column swaps
+    # under the model of the scheme the walk runs
+    assert auto.ordering in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER, A.PERM_ORDER_SEARCH)
+    assert auto.ops_per_step_walk <= min(deg.ops_per_step_walk, pap.ops_per_step_walk) + 1e-12
+    assert sorted(list(auto.col_order)[:36]) == list(range(36))
     assert pap.ops_per_step < pap.ops_per_step_paper
     assert sum(list(pap.group_size)[:36]) == 36
     # every row's group is the first ordered column that touches it
@@ -211,13 +215,41 @@ def test_slot_layout_groups_and_column0_rows_by_next_column():
 
 def test_generated_fp64_kernel_picks_the_cheaper_chain():
     """Generated FP64 kernels use two-state chains where the cost model says
-    they take fewer operations per step than the paired chain (the n=48 band:
-    column 0's rows are next touched late), and the paired chain otherwise (the
-    n=36 workload); PERM_FLAG_PAIRED_CHAIN forces the paired chain."""
+    they take fewer operations per step than the paired chain (the n=48 band,
+    the n=36 workload), and the paired chain where that is cheaper (a very
+    sparse ER matrix, where column 0 touches one row); PERM_FLAG_PAIRED_CHAIN
+    forces the paired chain; exact kernels keep one chain."""
     band = synth.band_plus(48, 3, 2, seed=3, values="f64")
     cfg2 = synth.single_er(36, 0.15, 2, values="f64")
+    sparse = synth.single_er(32, 0.05, 3, values="f64")
     assert "kDual = true" in A.codegen_source(band)
     assert "kDual = false" in A.codegen_source(band, flags=A.PERM_FLAG_PAIRED_CHAIN)
-    assert "kDual = false" in A.codegen_source(cfg2)
+    assert "kDual = true" in A.codegen_source(cfg2)
+    assert "kDual = false" in A.codegen_source(sparse)
     assert "kDual = false" in A.codegen_source(synth.band_plus(48, 3, 2, seed=3, values="01"))   # exact: one chain
+
+
+def test_order_search_lowers_the_walk_cost_model():
+    """The AUTO order search (walks of 2^30 steps and more) only accepts
+    column swaps that lower the cost model of the scheme the walk runs; its
+    result is a permutation of the columns and never costs more than the better
+    of DEGREE and PAPER.  Shorter walks keep that better order."""
+    cases = [(synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True), True),
+             (synth.band_plus(48, 3, 2, seed=3, values="f64"), True),
+             (synth.single_er(34, 0.2, 5, values="01"), False),
+             (synth.single_er(24, 0.2, 1, values="01"), False)]
+    for a, fp64 in cases:
+        n = a.shape[0]
+        auto = A.inspect(a)
+        base = min(A.inspect(a, ordering=o).ops_per_step_walk for o in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER))
+        assert sorted(list(auto.col_order)[:n]) == list(range(n))
+        assert auto.ops_per_step_walk <= base + 1e-12
+        if auto.ordering == A.PERM_ORDER_SEARCH:
+            assert auto.ops_per_step_walk < base
+        assert A.inspect(a, ordering=A.PERM_ORDER_SEARCH).ops_per_step_walk == auto.ops_per_step_walk
+    # the n=36 workload: 8.23 -> about 6.5 counted FP64 operations per step
+    cfg2 = A.inspect(cases[0][0])
+    assert cfg2.ordering == A.PERM_ORDER_SEARCH and cfg2.ops_per_step_walk < 7.0
+    short = synth.single_er(24, 0.2, 1, values="01")
+    assert A.inspect(short).ordering in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER)
 
