@@ -363,13 +363,16 @@ Layout choose_layout(const Matrix &m, int ordering_opt) {
     order_degree(m, cols);
     Layout deg = make_layout(m, cols, PERM_ORDER_DEGREE);
     Layout start = cost_per_step(deg, false) < cost_per_step(paper, false) ? deg : paper;
-    // AUTO / SEARCH: for walks of 2^30 steps and more (the generated kernels'
-    // range), refine the better order under the model of the scheme the walk
-    // will run.  The search takes about 0.2 ms of host time at n = 28, more
-    // than shorter walks would gain.
-    if (m.n < 31) return start;
+    // AUTO / SEARCH: for FP64 walks of 2^30 steps and more (the generated
+    // kernels' range), refine the better order under the model of the scheme
+    // the walk will run.  The search takes about 0.2 ms of host time at
+    // n = 28, more than shorter walks would gain; exact kernels fold runs of
+    // rows in 32 bits, which the one-chain model does not see (a searched
+    // order made the n=48 band's exact walk 7 % slower), so they keep the
+    // start order.
+    if (m.n < 31 || m.is_int) return start;
     for (int p = 0; p < m.n; ++p) cols[p] = start.col_order[p];
-    const bool fp64 = !m.is_int, long_walk = true;
+    const bool fp64 = true, long_walk = true;
     const double before = order_cost(m, cols, fp64, long_walk);
     search_order(m, cols, fp64, long_walk);
     if (!(order_cost(m, cols, fp64, long_walk) < before - 1e-12)) return start;
