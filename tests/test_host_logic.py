@@ -254,3 +254,41 @@ def test_order_search_lowers_the_walk_cost_model():
     exact_long = synth.single_er(34, 0.2, 5, values="01")   # exact walks keep the start order
     assert A.inspect(exact_long).ordering in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER)
 
+
+
+def _schedule_counts(a, ins):
+    """Per-step operation counts of the two chain schemes, by walking the Gray
+    schedule step by step (column j = ctz(l) flips at step l) and counting what
+    each step does, from the layout perm_inspect reports."""
+    n = a.shape[0]
+    co, ro = list(ins.col_order[:n]), list(ins.row_order[:n])
+    R = list(ins.group_size[:n])
+    nnz = [int(np.count_nonzero(a[:, c])) for c in co]
+    S = [0] * (n + 1)
+    for s in range(R[0]):
+        nxt = next((p for p in range(1, n - 1) if a[ro[s], co[p]] != 0), n - 1)
+        S[nxt] += 1
+    steps = (1 << (n - 1)) - 1
+    one_chain = two_state = 0.0
+    for l in range(1, steps + 1):
+        j = (l & -l).bit_length() - 1
+        # one chain: flip column j, rebuild levels j..0 (|R_0| + ... + |R_j| products), accumulate
+        one_chain += nnz[j] + sum(R[: j + 1]) + 1
+        if j == 0:
+            two_state += 2          # the odd step closes a pair: one difference, one accumulation
+        else:
+            two_state += nnz[j] + sum((R[m] + 1 if R[m] else 0) + 3 * S[m] for m in range(1, j + 1))
+    return one_chain / steps, two_state / steps
+
+
+def test_cost_models_match_a_step_by_step_count():
+    """The closed-form step-cost models (Lemma 2 weights) equal a direct count
+    over the Gray schedule: the one-chain model (perm_inspect ops_per_step) and
+    the two-state-chain model of short FP64 walks (ops_per_step_walk)."""
+    cases = [synth.single_er(12, 0.3, 1, values="f64"), synth.band_plus(14, 2, 1, seed=2, values="f64"),
+             synth.single_er(16, 0.2, 7, values="f64"), synth.ones(9).astype(np.float64)]
+    for a in cases:
+        ins = A.inspect(a)
+        one, two = _schedule_counts(a, ins)
+        assert abs(ins.ops_per_step - one) < 1e-9 * one, (ins.ops_per_step, one)
+        assert abs(ins.ops_per_step_walk - two) < 1e-9 * two, (ins.ops_per_step_walk, two)
