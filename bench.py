@@ -143,6 +143,52 @@ def cpu_baseline(a, seconds_hint: float = 15.0):
             "seconds": dt}
 
 
+def cpu_fp64_baseline(a, seconds_hint: float = 10.0):
+    """CPU-SparsePerman (cpu_sparseperman.c beside this file: FP64, degree-sorted
+    columns, zero tracking, every host core over aligned Gray chunks) on a
+    Gray prefix of the workload sized to about `seconds_hint` s."""
+    import ctypes
+    src = os.path.join(ROOT, "cpu_sparseperman.c")
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "libcpu_sparseperman.so")
+    subprocess.check_call(["gcc", "-O3", "-fPIC", "-shared", "-pthread", src, "-o", so, "-lm"])
+    L = ctypes.CDLL(so)
+    L.cpu_sparseperman_range.restype = ctypes.c_double
+    L.cpu_sparseperman_range.argtypes = [ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    n = a.shape[0]
+    order = sorted(range(n), key=lambda j: (int(np.count_nonzero(a[:, j])), j))   # ascending degree (Sec. VI-B)
+    ao = np.ascontiguousarray(a[:, order])
+    colptr, rows, vals = [0], [], []
+    for j in range(n):
+        nz = np.nonzero(ao[:, j])[0]
+        rows += list(nz)
+        vals += list(ao[nz, j])
+        colptr.append(len(rows))
+    colptr = np.array(colptr[:n], dtype=np.int32)
+    rows = np.array(rows, dtype=np.int32)
+    vals = np.array(vals, dtype=np.float64)
+    x0 = ao[:, n - 1] - ao.sum(axis=1) / 2.0
+    cores = os.cpu_count() or 1
+    K = 12
+    ab = ctypes.c_double()
+
+    def run(span):
+        t0 = time.perf_counter()
+        L.cpu_sparseperman_range(n, colptr.ctypes.data, rows.ctypes.data, vals.ctypes.data, x0.ctypes.data, 0, span,
+                                 K, cores, ctypes.byref(ab))
+        return time.perf_counter() - t0
+    k = 24
+    dt = run(1 << k)
+    while (1 << (k + 1)) * dt / (1 << k) < seconds_hint and k < n - 2:
+        k += 1
+        dt = run(1 << k)
+    return {"value": (1 << k) / dt, "unit": "steps/s", "cores": cores, "kind": "cpu-sparseperman (FP64)",
+            "sample": "Gray indices [0, 2^%d) of the n=36 matrix: FP64 Algorithm 1, degree-sorted columns, zero "
+                      "tracking, %d threads over aligned 2^%d-step chunks" % (k, cores, K),
+            "seconds": dt, "ms_per_permanent_extrapolated": 1e3 * dt * (1 << (n - 1 - k))}
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -169,6 +215,49 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def extras(A, sh, a, first):
+    """What the single-matrix line carries beside its headline (one GPU only):
+    the batch and serving workloads, accuracy against the oracle on every
+    workload, the first (cold) call on a matrix never seen before, and the
+    FP64 CPU baseline."""
+    from paper_2501_15126_gb300 import synth
+    out = {}
+    out["batch"] = measure_batch(A, sh)
+    out["serving"] = measure_serving(A)
+    # cold: a new n=36 matrix of the same shape, its kernel generated and compiled
+    b = synth.single_er(36, 0.15, 1002, values="f64", shuffle_cols=True)
+    t0 = time.perf_counter()
+    rb = A.permanent(b, stream=sh, flags=A.PERM_FLAG_NO_KERNEL_CACHE)
+    wall = time.perf_counter() - t0
+    out["e2e_cold"] = {"seconds": wall, "ms_plan": rb.ms_plan, "ms_compile": rb.ms_compile, "ms_kernel": rb.ms_kernel,
+                       "overhead_ms": rb.ms_plan + rb.ms_compile,
+                       "note": "a never-seen n=36 matrix through perm_plan_create (ordering, Algorithm 4, code "
+                               "generation, NVRTC) + perm_compute + perm_plan_destroy; the paper quotes < 2 s of "
+                               "generation and compilation per matrix (Sec. VI-F)"}
+    # accuracy against the oracle
+    golden = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "cfg2_n36.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            golden[k] = float(v)
+    want2 = golden["perm_hi"] + golden["perm_lo"]
+    a01 = synth.single_er(24, 0.2, 1, values="01")
+    _, af = synth.single_er_pair(24, 0.2, 1)
+    r01, rf = A.permanent(a01, stream=sh), A.permanent(af, stream=sh)
+    out["accuracy"] = {
+        "target": "exact results bit-identical, FP64 within 1e-9 relative to the oracle's permanent",
+        "cfg1_n24": {"exact_matches": r01.value == oracle_value(a01), "f64_rel_err": rel(rf.value, oracle_value(af)),
+                     "f64_precision": "double-double" if rf.precision == 2 else "fp64"},
+        "cfg2_n36": {"f64_rel_err": rel(first.value, want2),
+                     "kappa_sum_abs_terms_over_perm": golden["abs_terms"] / abs(want2),
+                     "reference": "oracle value stored in tests/golden/cfg2_n36.txt"},
+        "cfg4_batch_sampled": out["batch"].get("accuracy_vs_oracle"),
+        "cfg5_serving_sampled": out["serving"].get("accuracy_vs_oracle"),
+        "cfg3_n48": "whole 2^47-step exact walks: bench.py --workload cfg3 (profiles/cfg3_n48_full_permanent.md)"}
+    out["cpu_fp64_baseline"] = cpu_fp64_baseline(a)
+    return out
 
 
 def config_block(engine, steps_per_step):
@@ -271,169 +360,266 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, args.cpu_seconds)
+    if world == 1 and not args.no_extras:
+        line.update(extras(A, sh, a, first))
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_batch(args):
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def oracle_value(a):
+    """The oracle's permanent of a small matrix: Eq. 2 in integers for 0/1
+    inputs, Algorithm 1 in long double (all host cores) for real ones."""
+    import oracle
+    if a.dtype == np.int64:
+        return oracle.ryser_gray(a)
+    return float(oracle.nw_perm(a, threads=os.cpu_count() or 1)[0])
+
+
+def accuracy_sample(mats, results, values, max_n=22, count=40):
+    """Evenly spaced sample of the results with n <= max_n against the
+    oracle: exact mismatches, FP64 max relative error, FP64 results beyond 1e-9,
+    and how many of the sampled FP64 results came from double-double reruns."""
+    idx = [i for i, a in enumerate(mats) if a.shape[0] <= max_n]
+    f64 = [i for i in idx if values[i] != "01"][:: max(1, len([i for i in idx if values[i] != "01"]) // count)][:count]
+    ex = [i for i in idx if values[i] == "01"][:: max(1, len([i for i in idx if values[i] == "01"]) // count)][:count]
+    errs = [rel(results[i].value, oracle_value(mats[i])) for i in f64]
+    return {"f64_sampled": len(f64), "f64_max_rel_err": max(errs, default=0.0),
+            "f64_beyond_1e-9": sum(1 for e in errs if e > 1e-9),
+            "f64_double_double": sum(1 for i in f64 if results[i].precision == 2),
+            "exact_sampled": len(ex), "exact_mismatches": sum(1 for i in ex if results[i].value != oracle_value(mats[i])),
+            "sample": "every k-th matrix with n <= %d, up to %d per arithmetic" % (max_n, count)}
+
+
+def measure_batch(A, stream, count=10_000, steps=2, warmup=1, accuracy=True):
     """The 10,000-matrix workload: one persistent launch per kernel family
-    (perm_batch) against one plan and launch per matrix (perm_batch_sequential)."""
-    import torch
-    from paper_2501_15126_gb300 import _abi as A
+    (perm_batch) against one plan and launch per matrix (perm_batch_sequential,
+    the paper's policy) and against the best per-matrix form here (the
+    allocation-free call per matrix: no allocation, one launch and one sync)."""
     from paper_2501_15126_gb300 import synth
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    items = synth.batch(count=args.batch_count)
+    items = synth.batch(count=count)
     mats = [A.CSRMatrix(it.a) for it in items]
     steps_total = sum(1 << (it.n - 1) for it in items)
-    for _ in range(max(args.warmup, 1)):
-        A.batch(mats, stream=stream.cuda_stream)
+    for _ in range(max(warmup, 1)):
+        A.batch(mats, stream=stream)
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         t0 = time.perf_counter()
-        res = A.batch(mats, stream=stream.cuda_stream)
+        res = A.batch(mats, stream=stream)
         times.append(time.perf_counter() - t0)
-    # the two arithmetic halves on their own (each is its own kernel family)
     split = {}
     for vals in ("f64", "01"):
         sub = [m for m, it in zip(mats, items) if it.values == vals]
         sub_steps = sum(1 << (it.n - 1) for it in items if it.values == vals)
         t0 = time.perf_counter()
-        A.batch(sub, stream=stream.cuda_stream)
+        A.batch(sub, stream=stream)
         dt = time.perf_counter() - t0
         split[vals] = {"count": len(sub), "seconds": dt, "gray_steps_per_s": sub_steps / dt}
-    seq_t0 = time.perf_counter()
-    seq = A.batch(mats, sequential=True, stream=stream.cuda_stream)
-    seq_time = time.perf_counter() - seq_t0
+    t0 = time.perf_counter()
+    seq = A.batch(mats, sequential=True, stream=stream)
+    seq_time = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loop = [A.permanent_noalloc(m, stream=stream) for m in mats]
+    loop_time = time.perf_counter() - t0
     mism_exact = sum(1 for r, q, it in zip(res, seq, items) if it.values == "01" and r.value != q.value)
-    mism_f64 = sum(1 for r, q, it in zip(res, seq, items)
-                   if it.values == "f64" and abs(r.value - q.value) > 1e-9 * abs(q.value))
-    max_rel_f64 = max((abs(r.value - q.value) / abs(q.value) for r, q, it in zip(res, seq, items)
-                       if it.values == "f64"), default=0.0)
+    max_rel_f64 = max((rel(r.value, q.value) for r, q, it in zip(res, seq, items) if it.values == "f64"), default=0.0)
     best = min(times)
-    line = {"metric": "batched permanents/s (10,000 matrices, n in [12,28])", "value": len(items) / best,
-            "unit": "perms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * best, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+exact", "data": "synthetic",
-            "config": {"workload": "batch of %d ER matrices, n uniform in [12,28], p uniform in [0.2,0.4] + forced "
-                                   "diagonal, alternating 0/1 (exact) and (0,1] (FP64), seed 4" % len(items),
-                       "gray_steps_total": steps_total, "l2": "inputs re-uploaded every step"},
-            "gray_steps_per_s": steps_total / best, "by_arithmetic": split,
-            "sequential": {"seconds": seq_time, "perms_per_s": len(items) / seq_time,
-                           "note": "perm_batch_sequential: plan + launch + sync + destroy per matrix"},
-            "speedup_vs_sequential": seq_time / best,
-            "agreement_vs_sequential": {"exact_mismatches": mism_exact, "f64_beyond_1e-9": mism_f64,
-                                        "f64_max_rel_diff": max_rel_f64},
-            "kernel_ms": res[0].ms_kernel}
-    print(json.dumps(line))
-    return 0
+    out = {"metric": "batched permanents/s (10,000 matrices, n in [12,28])", "perms_per_s": len(items) / best,
+           "seconds": best, "gray_steps_total": steps_total, "gray_steps_per_s": steps_total / best,
+           "workload": "batch of %d ER matrices, n uniform in [12,28], p uniform in [0.2,0.4] + forced diagonal, "
+                       "alternating 0/1 (exact) and (0,1] (FP64), seed 4" % len(items),
+           "by_arithmetic": split,
+           "double_double_reruns": sum(1 for r in res if r.precision == 2),
+           "per_matrix_plans": {"seconds": seq_time, "perms_per_s": len(items) / seq_time,
+                                "speedup": seq_time / best,
+                                "note": "perm_batch_sequential: plan + launch + sync + destroy per matrix"},
+           "per_matrix_noalloc": {"seconds": loop_time, "perms_per_s": len(items) / loop_time,
+                                  "speedup": loop_time / best,
+                                  "note": "perm_compute_noalloc per matrix: no allocation, one walk launch and "
+                                          "one synchronisation per matrix"},
+           "agreement_vs_per_matrix": {"exact_mismatches": mism_exact, "f64_max_rel_diff": max_rel_f64}}
+    out["speedup_vs_best_per_matrix"] = min(seq_time, loop_time) / best
+    if accuracy:
+        out["accuracy_vs_oracle"] = accuracy_sample([it.a for it in items], res, [it.values for it in items])
+    return out
 
 
-def run_serving(args):
-    """Open-loop replay of the Poisson serving stream against the server, and
-    the same arrivals served by one plan + launch per request in order."""
-    import torch
-    from paper_2501_15126_gb300 import _abi as A
+def measure_serving(A, rate=2000.0, duration=60.0, sequential_seconds=10.0, accuracy=True):
+    """Open-loop replay of the Poisson stream against the server (latency from
+    each request's arrival), and the same requests' first `sequential_seconds`
+    served by one plan + launch per request, back to back (its capacity)."""
     from paper_2501_15126_gb300 import synth
-    torch.cuda.set_device(0)
-    reqs = synth.serving_stream(rate=args.rate, duration=args.duration, seed=5)
+    reqs = synth.serving_stream(rate=rate, duration=duration, seed=5)
     mats = [A.CSRMatrix(r.a) for r in reqs]
     arrivals = [r.t_arrival for r in reqs]
+    lat = [None] * len(reqs)
+    res = [None] * len(reqs)
+    with A.Server() as s:
+        for m in mats[:50]:                       # the kernel families set up
+            s.poll(s.submit(m), 60000)
+        tickets = [None] * len(reqs)
 
-    def replay_server():
-        lat = [None] * len(reqs)
-        res = [None] * len(reqs)
-        with A.Server() as s:
-            # warm the families up
-            for m in mats[:50]:
-                s.poll(s.submit(m), 60000)
-            tickets = [None] * len(reqs)
-            done_evt = threading.Event()
-
-            def collector():
-                for i in range(len(reqs)):
-                    while tickets[i] is None:
-                        time.sleep(0.0001)
-                    r = s.poll(tickets[i], -1)
-                    lat[i] = time.perf_counter() - (t0 + arrivals[i])
-                    res[i] = r
-                done_evt.set()
-            t0 = time.perf_counter()
-            th = threading.Thread(target=collector)
-            th.start()
-            for i, m in enumerate(mats):
-                delay = t0 + arrivals[i] - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                tickets[i] = s.submit(m)
-            th.join()
-            wall = time.perf_counter() - t0
-        return lat, res, wall
-
-    def replay_sequential():
-        lat = [None] * len(reqs)
-        res = [None] * len(reqs)
+        def collector():
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                res[i] = s.poll(tickets[i], -1)
+                lat[i] = time.perf_counter() - (t0 + arrivals[i])
         t0 = time.perf_counter()
+        th = threading.Thread(target=collector)
+        th.start()
         for i, m in enumerate(mats):
             delay = t0 + arrivals[i] - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            res[i] = A.permanent(m)
-            lat[i] = time.perf_counter() - (t0 + arrivals[i])
-        return lat, res, time.perf_counter() - t0
-
-    def capacity_server():
-        """Closed loop: every request submitted at once; time until all are done."""
-        with A.Server() as s:
-            for m in mats[:50]:
-                s.poll(s.submit(m), 60000)
-            t0 = time.perf_counter()
-            tickets = [s.submit(m) for m in mats]
-            for t in tickets:
-                s.poll(t, -1)
-            return len(mats) / (time.perf_counter() - t0)
-
-    def capacity_sequential():
-        t0 = time.perf_counter()
-        for m in mats:
-            A.permanent(m)
-        return len(mats) / (time.perf_counter() - t0)
-
-    ls, rs, ws = replay_server()
-    lq, rq, wq = replay_sequential()
-    cap_s = capacity_server()
-    cap_q = capacity_sequential()
+            tickets[i] = s.submit(m)
+        th.join()
+        wall = time.perf_counter() - t0
+        # capacity: the first `sequential_seconds` of requests submitted at once
+        nseq = sum(1 for t in arrivals if t < sequential_seconds)
+        t1 = time.perf_counter()
+        for t in [s.submit(m) for m in mats[:nseq]]:
+            s.poll(t, -1)
+        cap_server = nseq / (time.perf_counter() - t1)
+    t1 = time.perf_counter()
+    seq = [A.permanent(m) for m in mats[:nseq]]
+    cap_seq = nseq / (time.perf_counter() - t1)
     q = lambda v, p: float(np.percentile(np.array(v) * 1e3, p))
-    bad = [(i, reqs[i].a.shape[0], reqs[i].values, a.status, a.value, b.value) for i, (a, b) in enumerate(zip(rs, rq))
-           if a.status or b.status or (a.value != b.value if a.vtype == 1 else abs(a.value - b.value) > 1e-9 * abs(b.value))]
-    mism = len(bad)
+    mism = sum(1 for r, z in zip(res[:nseq], seq) if r.status or z.status or
+               (r.value != z.value if r.vtype == 1 else rel(r.value, z.value) > 1e-9))
+    out = {"metric": "served permanents/s with p50/p99 latency (Poisson %g req/s)" % rate,
+           "perms_per_s": len(reqs) / wall, "requests": len(reqs), "seconds": wall,
+           "p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "max_ms": q(lat, 100),
+           "failed": sum(1 for r in res if r.status != 0),
+           "double_double_reruns": sum(1 for r in res if r.precision == 2),
+           "workload": "Poisson arrivals at %g req/s for %g s, n = 16 + m with P(m) ~ 2^-m up to 40, p uniform in "
+                       "[0.1,0.3] + diagonal, mixed 0/1 and (0,1], seed 5" % (rate, duration),
+           "capacity_perms_per_s": {"server": cap_server, "per_request_plans": cap_seq, "ratio": cap_server / cap_seq,
+                                    "requests": nseq,
+                                    "note": "the first %g s of requests submitted at once; per_request_plans: "
+                                            "plan + launch + sync + destroy per request, back to back"
+                                            % sequential_seconds},
+           "agreement_vs_per_request": {"mismatches": mism, "compared": nseq}}
+    if accuracy:
+        out["accuracy_vs_oracle"] = accuracy_sample([r.a for r in reqs], res, [r.values for r in reqs], count=60)
+    return out
 
-    def terms_bound(a):
-        # sum of |Nijenhuis-Wilf terms| <= 2^(n-1) prod_i (sum_j |a_ij| / 2) = prod_i rowsum_i / 2
-        return float(np.prod(np.abs(a).sum(axis=1))) / 2.0
 
-    # FP64 differences beyond 1e-9 relative that are also beyond 1e-12 of the a-priori bound on
-    # sum |terms| (64 n u sum|terms| < 1e-12 sum|terms| for n <= 48): an ill-conditioned permanent
-    # (heavy cancellation) cannot be resolved to 1e-9 of itself in FP64 by any summation order
-    beyond_bound = sum(1 for i, n, v, _, x, y in bad
-                       if v != "01" and abs(x - y) > 1e-12 * terms_bound(reqs[i].a))
-    line = {"metric": "served permanents/s with p50/p99 latency (Poisson 2,000 req/s)",
-            "value": len(reqs) / ws, "unit": "perms/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+exact", "data": "synthetic",
-            "config": {"workload": "Poisson arrivals at %g req/s for %g s (%d requests), n = 16 + m with P(m) ~ 2^-m "
-                                   "up to 40, p uniform in [0.1,0.3] + diagonal, mixed 0/1 and (0,1], seed 5"
-                                   % (args.rate, args.duration, len(reqs))},
-            "p50_ms": q(ls, 50), "p99_ms": q(ls, 99), "max_ms": q(ls, 100),
-            "sequential": {"perms_per_s": len(reqs) / wq, "p50_ms": q(lq, 50), "p99_ms": q(lq, 99),
-                           "max_ms": q(lq, 100)},
-            "capacity_perms_per_s": {"server": cap_s, "sequential": cap_q, "ratio": cap_s / cap_q,
-                                     "note": "closed loop: the same requests submitted all at once"},
-            "mismatches_vs_sequential": mism, "mismatch_examples": [list(map(str, b)) for b in bad[:5]],
-            "f64_mismatches_beyond_terms_bound": beyond_bound}
-    print(json.dumps(line))
+def run_batch(args):
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    print(json.dumps(measure_batch(A, stream.cuda_stream, args.batch_count, args.steps, args.warmup)))
+    return 0
+
+
+def run_serving(args):
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    torch.cuda.set_device(0)
+    print(json.dumps(measure_serving(A, args.rate, args.duration)))
+    return 0
+
+
+def run_cfg3(args):
+    """The n=48 band workload in full (2^47 Gray steps per permanent), exact,
+    through checkpointed slices: the band |i-j| <= 3 plus 2 off-band nonzeros
+    per row (0/1) in the Algorithm 3 order and in the degree order -- the
+    permanent does not depend on the column order (Sec. V), so the two must be
+    the same integer -- and its band-only sibling, checked against the banded
+    dynamic program of the oracle.  Checkpoint files go to --ckpt-dir, so an
+    interrupted run resumes where it stopped."""
+    import torch
+    import oracle
+    from paper_2501_15126_gb300 import _abi as A
+    from paper_2501_15126_gb300 import synth
+    torch.cuda.set_device(0)
+    os.makedirs(args.ckpt_dir, exist_ok=True)
+    a01 = synth.band_plus(48, 3, 2, seed=3, values="01")
+    band = synth.band_plus(48, 3, 0, seed=3, values="01")
+    runs = [("band_offband_alg3", a01, A.PERM_ORDER_PAPER), ("band_offband_degree", a01, A.PERM_ORDER_DEGREE),
+            ("band_only", band, A.PERM_ORDER_AUTO)]
+    out = {"workload": "n=48 band |i-j|<=3 + 2 off-band nonzeros per row, 0/1 values, seed 3 (and its band-only "
+                       "sibling); whole 2^47-step walks, exact", "slice_log2": args.slice_log2, "runs": {}}
+    for name, a, order in runs:
+        path = os.path.join(args.ckpt_dir, "cfg3_%s.ckpt" % name)
+        t0 = time.time()
+        st, r = A.checkpoint_run(a, path, slice_log2=args.slice_log2, max_slices=args.max_slices,
+                                 ordering=order, engine=A.PERM_ENGINE_CODEGEN)
+        rec = {"status": "done" if st == A.PERM_OK else "partial", "gray_steps_done": r.steps,
+               "wall_s_this_call": time.time() - t0, "kernel_s_this_call": r.ms_kernel / 1e3,
+               "ordering": r.ordering, "exact_words": r.exact_words}
+        if st == A.PERM_OK:
+            rec["permanent"] = str(r.value)
+            if name == "band_only":
+                want = oracle.band_dp_int(a, 3)
+                rec["band_dp"] = str(want)
+                rec["matches_band_dp"] = r.value == want
+        out["runs"][name] = rec
+        print(json.dumps({name: rec}), flush=True)
+    ra, rd = out["runs"]["band_offband_alg3"], out["runs"]["band_offband_degree"]
+    if "permanent" in ra and "permanent" in rd:
+        out["orders_agree"] = ra["permanent"] == rd["permanent"]
+    print(json.dumps(out))
+    return 0
+
+
+def run_ablation(args):
+    """The paper's ablation (Sec. VI-B, Table III, Fig. 4) on GB300: the
+    library's generated kernel (product chain, two-state chains) against
+    CodeGen-PureReg (a full product every step, x in registers) and
+    GPU-SparsePerman (x in shared memory, a full product every step, zero
+    tracking), on the n=36 workload (whole walk) and an n=40 ER p=0.1 matrix
+    (the paper's smallest Table III shape; a 2^36-step prefix).  Kernel time by
+    CUDA events (best of 3 after a warm-up), all in FP64; then the host-only
+    ordering report of Fig. 4 (register rows k and columns c of Algorithm 4,
+    and operations per step, without and with Algorithm 3)."""
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    from paper_2501_15126_gb300 import synth
+    torch.cuda.set_device(0)
+    cases = [("n36_workload", workload_matrix(), 0, 0),
+             ("n40_er_p0.1", synth.single_er(40, 0.1, 40, values="f64"), 0, 1 << 36)]
+    engines = [("codegen_chain", dict(engine=A.PERM_ENGINE_CODEGEN)),
+               ("codegen_pure_reg", dict(engine=A.PERM_ENGINE_CODEGEN, flags=A.PERM_FLAG_PURE_REG)),
+               ("generic_chain", dict(engine=A.PERM_ENGINE_GENERIC)),
+               ("x_shared", dict(engine=A.PERM_ENGINE_XSHARED, ordering=A.PERM_ORDER_DEGREE))]
+    out = {"workload": "ablation", "cases": {}}
+    for name, a, lo, hi in cases:
+        rec = {}
+        for ename, kw in engines:
+            p = A.Plan(a, g_lo=lo, g_hi=hi, precision=A.PERM_PREC_F64, **kw)
+            r = p.compute()
+            ms = min(p.compute().ms_kernel for _ in range(3))
+            rec[ename] = {"ms": ms, "gray_steps_per_s": r.steps / (ms / 1e3), "value": r.value,
+                          "ops_per_step_model": r.fp_ops_per_step, "regs": r.regs_per_thread,
+                          "threads": r.threads, "zero_skip_frac": r.zero_skip_frac}
+            p.close()
+        base = rec["codegen_chain"]["ms"]
+        for ename in rec:
+            rec[ename]["chain_speedup_over_this"] = rec[ename]["ms"] / base
+        vals = [rec[e]["value"] for e in rec]
+        rec["max_rel_spread_of_values"] = (max(vals) - min(vals)) / abs(vals[0])
+        rec["gray_steps"] = (hi - lo) if hi else 1 << (a.shape[0] - 1)
+        out["cases"][name] = rec
+        print(json.dumps({name: rec}), flush=True)
+    fig4 = {}
+    for name, a, _, _ in cases:
+        rows = {}
+        for oname, o in (("none", A.PERM_ORDER_NONE), ("degree", A.PERM_ORDER_DEGREE), ("algorithm3", A.PERM_ORDER_PAPER)):
+            ins = A.inspect(a, ordering=o)
+            rows[oname] = {"reg_rows_k": ins.reg_rows, "reg_cols_c": ins.reg_cols,
+                           "ops_per_step_chain": ins.ops_per_step, "ops_per_step_full_product": ins.ops_per_step_paper,
+                           "ops_per_step_walk": ins.ops_per_step_walk}
+        fig4[name] = rows
+    out["fig4_ordering"] = fig4
+    print(json.dumps(out))
     return 0
 
 
@@ -474,8 +660,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single workload: only the headline (no batch, serving, accuracy, cold e2e, FP64 CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile", "cfg3", "ablation"])
+    ap.add_argument("--ckpt-dir", default="gpurun_out/cfg3_ckpt", help="cfg3: checkpoint files")
+    ap.add_argument("--slice-log2", type=int, default=40, help="cfg3: Gray indices per checkpointed slice (log2)")
+    ap.add_argument("--max-slices", type=int, default=0, help="cfg3: slices per run per call (0 = all)")
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
     ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
@@ -498,6 +689,10 @@ def main():
         return run_serving(args)
     if args.workload == "profile":
         return run_profile_case(args)
+    if args.workload == "cfg3":
+        return run_cfg3(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     return run_ours(args)
 
 

@@ -99,15 +99,40 @@ enum {
 enum {
     PERM_ENGINE_AUTO = 0,     /* codegen for single large matrices, generic otherwise     */
     PERM_ENGINE_GENERIC = 1,  /* precompiled kernels, matrix read from shared memory      */
-    PERM_ENGINE_CODEGEN = 2   /* per-matrix CUDA C++ generated and compiled with NVRTC    */
+    PERM_ENGINE_CODEGEN = 2,  /* per-matrix CUDA C++ generated and compiled with NVRTC    */
+    PERM_ENGINE_XSHARED = 3   /* the GPU-SparsePerman baseline of Sec. VI-B (an ablation): */
+                              /*   x in shared memory, columns read from a CSC image, zero */
+                              /*   tracking, the product of all n rows at every step;      */
+                              /*   FP64 inputs only                                         */
+};
+
+/* Arithmetic of the FP64 path (integer inputs are always exact).  The walk's
+   sum alternates in sign (Sec. II), so its rounding error is about
+   n 2^-53 sum_g |term_g|, which can be far above 2^-53 |perm| when the terms
+   cancel.  Double-double arithmetic (every x_i, product and sum an unevaluated
+   pair of doubles, FMA-based exact products) lowers that to a few 2^-104
+   sum_g |term_g|, at several times the FP64 cost. */
+enum {
+    PERM_PREC_AUTO = 0,  /* FP64; a whole walk of n <= 32 whose estimate n 2^-53 sum|terms| / |perm|  */
+                         /*   exceeds 1e-10 (or whose FP64 result is 0) is rerun in double-double      */
+    PERM_PREC_F64 = 1,   /* FP64 only                                                                */
+    PERM_PREC_DD = 2     /* double-double (generic kernels, n <= 48)                                  */
 };
 
 /* Option flags. */
 enum {
     PERM_FLAG_NO_KERNEL_CACHE = 1,  /* codegen: compile even if this source was compiled before */
     PERM_FLAG_NO_GRAPH = 2,         /* perm_compute: never replay the plan as a CUDA graph     */
-    PERM_FLAG_PAIRED_CHAIN = 4      /* codegen FP64: the paired chain even where the two-state */
+    PERM_FLAG_PAIRED_CHAIN = 4,     /* codegen FP64: the paired chain even where the two-state */
                                     /*   chains cost fewer operations per step                 */
+    PERM_FLAG_PURE_REG = 8,         /* codegen: the paper's CodeGen-PureReg scheme (Sec. III-B,*/
+                                    /*   Listings 2-3): every row of x in registers and the    */
+                                    /*   product of all n rows at every step (no product      */
+                                    /*   chain, no zero skip); an ablation baseline            */
+    PERM_FLAG_ABS_SUM = 16          /* codegen FP64: accumulate abs_term_sum even where it is  */
+                                    /*   not needed (it costs about a tenth of the speed of a  */
+                                    /*   generated FP64 kernel; the generic kernels always     */
+                                    /*   keep it)                                               */
 };
 
 /* Options; a zeroed struct (or NULL) means "choose automatically". */
@@ -133,7 +158,8 @@ typedef struct {
     int32_t timeout_ms;    /* device-side deadline for one compute: warps stop taking work */
                            /*   once the GPU clock passes it, and the call returns         */
                            /*   PERM_ERR_TIMEOUT (the context stays usable); 0 = none      */
-    int32_t reserved1;
+    int32_t precision;     /* PERM_PREC_*: arithmetic of FP64 inputs (sub-ranges and       */
+                           /*   checkpointed runs: AUTO means FP64)                         */
 } perm_opts_t;
 
 /* Result of one permanent (or one Gray sub-range). */
@@ -163,6 +189,18 @@ typedef struct {
     double ms_kernel;      /* device time of the walk + reduction (CUDA events)       */
     double fp_ops_per_step;/* counted arithmetic ops per Gray step (cost model)       */
     double zero_skip_frac; /* fraction of 2^B-step blocks skipped as all-zero         */
+    /* FP64 inputs: sum over the walk's Gray indices of |prod_i x_i(g)|, times 2 for
+       a whole walk (the scale of the permanent), raw for a sub-range.  It is
+       accumulated in FP32 on the GPU (relative accuracy about 1e-5); terms below
+       2^-246 of the a-priori largest term are not counted.  abs_term_sum / |perm|
+       is the cancellation of the alternating sum (Sec. II): an FP64 result is good
+       to about n 2^-53 of it, a double-double one to about 2^-100 of it.  0 for
+       integer inputs, and 0 (not computed) from a generated FP64 kernel of n > 32,
+       a sub-range or precision F64 unless PERM_FLAG_ABS_SUM is set.          */
+    double abs_term_sum;
+    int32_t precision;     /* FP64 inputs: PERM_PREC_F64 or PERM_PREC_DD that produced */
+                           /*   the value; 0 for integer inputs                         */
+    int32_t reserved2;
 } perm_result_t;
 
 typedef struct perm_plan_s *perm_plan_t;
@@ -239,6 +277,8 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal                                        */
     int32_t timeout_ms;       /* a request unfinished after this long fails with TIMEOUT;  */
                               /*   0 = none                                                 */
+    int32_t precision;        /* PERM_PREC_* for FP64 requests (AUTO: an ill-conditioned    */
+                              /*   request is requeued once as a double-double request)    */
 } perm_server_opts_t;
 
 /* Starts a serving loop: a host thread that admits submitted matrices into
@@ -318,12 +358,20 @@ perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opt
    the ALU roofline denominators of the FP64 and exact walks. */
 perm_status_t perm_issue_rates(void *stream, double *fp64_ops_per_s, double *imad_ops_per_s);
 
-/* The DFMA issue rate with every instruction guarded by a predicate that is
-   true (issued_on) or false (issued_off) in every lane: on GB300 the two are
-   equal, i.e. a false predicate does not free the FP64 pipe, which is why the
-   generic kernels dispatch to touched register slots instead of predicating
-   over all of them. */
-perm_status_t perm_fp64_predication_rates(void *stream, double *issued_on, double *issued_off);
+/* --------------------------------------------------- failure injection */
+/* For tests of the failure paths, without any GPU fault: the next `count`
+   calls the library makes at `site` are treated as failed (the call is not
+   made; the library takes its error path exactly as for a real failure).
+   count = 0 clears the site.  Sites: */
+enum {
+    PERM_SITE_WAVE_LAUNCH = 1,  /* serving: launch of a wave of the generic walk -> its      */
+                                /*   requests fail with PERM_ERR_CUDA                        */
+    PERM_SITE_NVRTC = 2,        /* codegen: NVRTC compile -> PERM_ERR_NVRTC                  */
+    PERM_SITE_FINISH = 3,       /* serving: a final reduction -> its requests fail           */
+    PERM_SITE_UPLOAD = 4,       /* serving: a request's matrix image upload -> it fails      */
+    PERM_SITE_LAUNCH = 5        /* perm_compute: the walk launch -> PERM_ERR_CUDA            */
+};
+perm_status_t perm_debug_inject_failures(int32_t site, int32_t count);
 
 /* ------------------------------------------------------------- misc */
 

@@ -20,10 +20,14 @@ PERM_OK, PERM_ERR_ARG, PERM_ERR_SIZE, PERM_ERR_PATTERN, PERM_ERR_OVERFLOW, PERM_
 PERM_F64, PERM_I64 = 0, 1
 PERM_CSR, PERM_CSC = 0, 1
 PERM_ORDER_AUTO, PERM_ORDER_NONE, PERM_ORDER_DEGREE, PERM_ORDER_PAPER, PERM_ORDER_SEARCH = 0, 1, 2, 3, 4
-PERM_ENGINE_AUTO, PERM_ENGINE_GENERIC, PERM_ENGINE_CODEGEN = 0, 1, 2
+PERM_ENGINE_AUTO, PERM_ENGINE_GENERIC, PERM_ENGINE_CODEGEN, PERM_ENGINE_XSHARED = 0, 1, 2, 3
 PERM_FLAG_NO_KERNEL_CACHE = 1
 PERM_FLAG_NO_GRAPH = 2
 PERM_FLAG_PAIRED_CHAIN = 4
+PERM_FLAG_PURE_REG = 8
+PERM_FLAG_ABS_SUM = 16
+PERM_PREC_AUTO, PERM_PREC_F64, PERM_PREC_DD = 0, 1, 2
+PERM_SITE_WAVE_LAUNCH, PERM_SITE_NVRTC, PERM_SITE_FINISH, PERM_SITE_UPLOAD, PERM_SITE_LAUNCH = 1, 2, 3, 4, 5
 
 c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
 
@@ -36,7 +40,7 @@ class Matrix(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("ordering", c_i32), ("engine", c_i32), ("reg_rows", c_i32), ("chunk_log2", c_i32),
                 ("threads", c_i32), ("exact_words", c_i32), ("zero_skip", c_i32), ("flags", c_i32),
-                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64), ("timeout_ms", c_i32), ("reserved1", c_i32)]
+                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64), ("timeout_ms", c_i32), ("precision", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -45,7 +49,8 @@ class Result(ctypes.Structure):
                 ("exact_words", c_i32), ("engine", c_i32), ("ordering", c_i32), ("reg_rows", c_i32),
                 ("reg_cols", c_i32), ("chunk_log2", c_i32), ("threads", c_i32), ("regs_per_thread", c_i32),
                 ("steps", c_u64), ("ms_plan", c_dbl), ("ms_compile", c_dbl), ("ms_kernel", c_dbl),
-                ("fp_ops_per_step", c_dbl), ("zero_skip_frac", c_dbl)]
+                ("fp_ops_per_step", c_dbl), ("zero_skip_frac", c_dbl), ("abs_term_sum", c_dbl),
+                ("precision", c_i32), ("reserved2", c_i32)]
 
     @property
     def exact(self) -> int:
@@ -73,7 +78,7 @@ class Inspect(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_inflight", c_i32), ("max_n", c_i32), ("step_budget", c_dbl), ("device", c_i32),
-                ("timeout_ms", c_i32)]
+                ("timeout_ms", c_i32), ("precision", c_i32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -108,8 +113,8 @@ SIGNATURES = [
     ("perm_version", ctypes.c_char_p, []),
     ("perm_sizeof", c_i64, [c_i32]),
     ("perm_issue_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
-    ("perm_fp64_predication_rates", c_i32, [c_vp, ctypes.POINTER(c_dbl), ctypes.POINTER(c_dbl)]),
     ("perm_compute_noalloc", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), c_vp, ctypes.POINTER(Result)]),
+    ("perm_debug_inject_failures", c_i32, [c_i32, c_i32]),
     ("perm_checkpoint_run", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), ctypes.c_char_p, c_i32, c_i32, c_vp,
                                     ctypes.POINTER(Result)]),
 ]
@@ -273,8 +278,8 @@ def issue_rates(stream: int = 0):
 class Server:
     """perm_server_create / perm_submit / perm_poll / perm_server_destroy."""
 
-    def __init__(self, max_inflight=0, max_n=0, step_budget=0.0, device=0, timeout_ms=0):
-        o = ServerOpts(max_inflight, max_n, step_budget, device, timeout_ms)
+    def __init__(self, max_inflight=0, max_n=0, step_budget=0.0, device=0, timeout_ms=0, precision=0):
+        o = ServerOpts(max_inflight, max_n, step_budget, device, timeout_ms, precision)
         h = c_vp()
         check(lib().perm_server_create(ctypes.byref(o), ctypes.byref(h)), "perm_server_create")
         self.h = h
@@ -320,11 +325,9 @@ class Server:
             pass
 
 
-def fp64_predication_rates(stream: int = 0):
-    """(DFMA/s with a true predicate, DFMA/s with a false predicate)."""
-    a, b = c_dbl(), c_dbl()
-    check(lib().perm_fp64_predication_rates(c_vp(stream), ctypes.byref(a), ctypes.byref(b)), "predication rates")
-    return a.value, b.value
+def inject_failures(site: int, count: int):
+    """perm_debug_inject_failures: the next `count` calls at `site` take their error path."""
+    check(lib().perm_debug_inject_failures(site, count), "perm_debug_inject_failures")
 
 
 def batch(mats, sequential: bool = False, stream: int = 0, **kw):

@@ -19,8 +19,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libperm.so")
 
 SOURCES = ["host.cpp", "api.cpp", "codegen.cpp", "batch.cpp", "tune.cpp", "server.cpp", "generic.cu",
-           "generic_f64.cu", "generic_r64.cu", "generic_r96.cu", "generic_r128.cu", "generic_r160.cu",
-           "generic_r192.cu", "microbench.cu", "noalloc.cu", "checkpoint.cpp"]
+           "generic_f64.cu", "generic_dd.cu", "generic_r64.cu", "generic_r96.cu", "generic_r128.cu", "generic_r160.cu",
+           "generic_r192.cu", "microbench.cu", "noalloc.cu", "checkpoint.cpp", "xshared.cu"]
 EMBED = ["core.cuh", "devmat.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

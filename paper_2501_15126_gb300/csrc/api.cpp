@@ -1,6 +1,7 @@
 // api.cpp -- the C ABI of libperm (see include/perm.h): plans, compute,
 // inspection helpers.  Batch and serving live in batch.cpp / server.cpp.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstddef>
@@ -64,10 +65,17 @@ typedef pk::DevMat<48, double> DevMat48F;
 static_assert(offsetof(DevMat16F, x0) == 48 + 12 * 16, "image header");
 static_assert(offsetof(DevMat32I, x0) == 48 + 12 * 32, "image header");
 static_assert(offsetof(DevMat48F, x0) == 48 + 12 * 48, "image header");
+struct HostDD { double h, l; };
+static_assert(offsetof(DevMat48F, val) == 48 + 12 * 48 + 8 * 48, "image values");
+typedef pk::DevMat<32, double, HostDD> DevMat32DD;
+static_assert(offsetof(DevMat32DD, val) == 48 + 12 * 32 + 16 * 32, "double-double image values");
 
-size_t devmat_bytes(int arith, int nmax, int nnz) {
-    const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
-    const size_t b = devmat_head(nmax) + vsz * (size_t)nmax + vsz * (size_t)nnz;
+// value and start-value sizes of an image layout (kImgF64, kImgInt, kImgDD)
+static size_t img_vsz(int img) { return img == kImgInt ? sizeof(int) : sizeof(double); }
+static size_t img_x0sz(int img) { return img == kImgDD ? 2 * sizeof(double) : img_vsz(img); }
+
+size_t devmat_bytes(int img, int nmax, int nnz) {
+    const size_t b = devmat_head(nmax) + img_x0sz(img) * (size_t)nmax + img_vsz(img) * (size_t)nnz;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -77,19 +85,37 @@ static int devmat_nnz(const Layout &L) {
     return nnz;
 }
 
-size_t devmat_bytes_for(const Layout &L, int arith, int nmax) { return devmat_bytes(arith, nmax, devmat_nnz(L)); }
+size_t devmat_bytes_for(const Layout &L, int img, int nmax) { return devmat_bytes(img, nmax, devmat_nnz(L)); }
 
-void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img) {
-    img.assign(devmat_bytes(arith, nmax, devmat_nnz(L)), 0);
-    build_devmat_into(m, L, arith, nmax, img.data());
+void build_devmat(const Matrix &m, const Layout &L, int img, int nmax, std::vector<unsigned char> &out) {
+    out.assign(devmat_bytes(img, nmax, devmat_nnz(L)), 0);
+    build_devmat_into(m, L, img, nmax, out.data());
 }
 
-void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, unsigned char *dst) {
+// x0_i = a_{i,last} - (1/2) sum_j a_ij as an exact double-double (hi, lo):
+// halving is exact and every partial sum is accumulated with TwoSum, so no bit
+// is lost while the value fits 106 bits (values on a common 2^-53 grid do).
+static void x0_dd(const Matrix &m, int r, int last, double *hi_out, double *lo_out) {
+    double hi = 0.0, lo = 0.0;
+    auto add = [&](double v) {
+        const double s = hi + v;
+        const double bb = s - hi;
+        lo += (hi - (s - bb)) + (v - bb);
+        hi = s;
+    };
+    for (int j = 0; j < m.n; ++j) add(-0.5 * m.fval(r, j));
+    add(m.fval(r, last));
+    const double s = hi + lo;
+    *lo_out = lo - (s - hi);
+    *hi_out = s;
+}
+
+void build_devmat_into(const Matrix &m, const Layout &L, int img, int nmax, unsigned char *dst) {
     const int n = m.n;
     const int last = L.col_order[n - 1];
-    const size_t vsz = arith == 0 ? sizeof(double) : sizeof(int);
+    const size_t vsz = img_vsz(img), x0sz = img_x0sz(img);
     const int nnz = devmat_nnz(L);
-    const size_t bytes = devmat_bytes(arith, nmax, nnz);
+    const size_t bytes = devmat_bytes(img, nmax, nnz);
     std::memset(dst, 0, bytes);
     int32_t *hdr = reinterpret_cast<int32_t *>(dst);
     hdr[0] = n;
@@ -104,10 +130,14 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
     for (int g = 0; g <= n; ++g) gbegin[g] = (uint8_t)L.group_begin[g];
     for (int g = 0; g <= n; ++g) sbegin[g] = (uint8_t)L.s_begin[g];
     unsigned char *x0 = dst + devmat_head(nmax);
-    unsigned char *val = x0 + vsz * nmax;
+    unsigned char *val = x0 + x0sz * nmax;
     for (int s = 0; s < n; ++s) {
         const int r = L.row_order[s];
-        if (arith == 0) {
+        if (img == kImgDD) {
+            double v[2];
+            x0_dd(m, r, last, &v[0], &v[1]);
+            std::memcpy(x0 + x0sz * s, v, x0sz);
+        } else if (img == kImgF64) {
             double rowsum = 0.0;
             for (int j = 0; j < n; ++j) rowsum += m.fval(r, j);
             const double v = m.fval(r, last) - rowsum / 2.0;
@@ -127,10 +157,47 @@ void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, un
             if (!((L.colmask[p] >> s) & 1ull)) continue;
             const int r = L.row_order[s];
             unsigned char *d = val + vsz * (size_t)k++;
-            if (arith == 0) { const double v = m.fval(r, c); std::memcpy(d, &v, vsz); }
+            if (img != kImgInt) { const double v = m.fval(r, c); std::memcpy(d, &v, vsz); }
             else { const int v = (int)(2 * m.ival(r, c)); std::memcpy(d, &v, vsz); }
         }
     }
+}
+
+// The CSC image of the x-in-shared-memory baseline (xshared.cu): header
+// (n, nnz, bytes, 0), colptr[n] and rows[nnz] (int32, original rows), then
+// 8-byte aligned x0[n] and vals[nnz]; columns are positions 0..n-2 of the
+// plan's order, x0 by original row.
+void build_xshared_image(const perm_plan_s &P, std::vector<unsigned char> &img) {
+    const Matrix &m = P.m;
+    const int n = m.n;
+    const int last = P.L.col_order[n - 1];
+    std::vector<int32_t> colptr(n, 0), rows;
+    std::vector<double> vals;
+    for (int p = 0; p + 1 < n; ++p) {
+        colptr[p] = (int32_t)rows.size();
+        const int c = P.L.col_order[p];
+        for (int i = 0; i < n; ++i)
+            if (m.nz(i, c)) { rows.push_back(i); vals.push_back(m.fval(i, c)); }
+    }
+    colptr[n - 1] = (int32_t)rows.size();
+    const int nnz = (int)rows.size();
+    size_t off = 16 + 4 * (size_t)(n + nnz);
+    off = (off + 7) & ~(size_t)7;
+    const size_t bytes = (off + 8 * (size_t)(n + nnz) + 15) & ~(size_t)15;
+    img.assign(bytes, 0);
+    int32_t *h = reinterpret_cast<int32_t *>(img.data());
+    h[0] = n;
+    h[1] = nnz;
+    h[2] = (int32_t)bytes;
+    std::memcpy(h + 4, colptr.data(), 4 * (size_t)n);
+    if (nnz) std::memcpy(h + 4 + n, rows.data(), 4 * (size_t)nnz);
+    double *x0 = reinterpret_cast<double *>(img.data() + off);
+    for (int i = 0; i < n; ++i) {
+        double rowsum = 0.0;
+        for (int j = 0; j < n; ++j) rowsum += m.fval(i, j);
+        x0[i] = m.fval(i, last) - rowsum / 2.0;
+    }
+    if (nnz) std::memcpy(x0 + n, vals.data(), 8 * (size_t)nnz);
 }
 
 // Checks that the exact walk's doubled row sums fit int32.
@@ -169,12 +236,19 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
         return fail(PERM_ERR_ARG, "sub-range ends must be multiples of 32");
     if (opts.ordering < 0 || opts.ordering > PERM_ORDER_SEARCH) return fail(PERM_ERR_ARG, "bad ordering");
     if (opts.ordering == PERM_ORDER_SEARCH) opts.ordering = PERM_ORDER_AUTO;
-    if (opts.engine < 0 || opts.engine > PERM_ENGINE_CODEGEN) return fail(PERM_ERR_ARG, "bad engine");
+    if (opts.engine < 0 || opts.engine > PERM_ENGINE_XSHARED) return fail(PERM_ERR_ARG, "bad engine");
+    if (opts.engine == PERM_ENGINE_XSHARED && A->vtype != PERM_F64)
+        return fail(PERM_ERR_ARG, "the x-in-shared-memory baseline takes FP64 inputs only");
     if (opts.exact_words < 0 || opts.exact_words > 3) return fail(PERM_ERR_ARG, "exact_words must be 0..3");
     if (opts.chunk_log2 < 0 || opts.chunk_log2 > 63) return fail(PERM_ERR_ARG, "bad chunk_log2");
     if (opts.threads < 0) return fail(PERM_ERR_ARG, "threads < 0");
     if (opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
+    if (opts.precision < PERM_PREC_AUTO || opts.precision > PERM_PREC_DD) return fail(PERM_ERR_ARG, "bad precision");
     P.zero = !has_perfect_matching(P.m);
+    if (!P.m.is_int) {
+        P.abs_shift = abs_shift_for(P.m);
+        P.dd = opts.precision == PERM_PREC_DD;
+    }
     P.L = choose_layout(P.m, opts.ordering);
     P.ops_per_step = cost_per_step(P.L, false);
     P.ops_per_step_paper = cost_per_step(P.L, true);
@@ -276,10 +350,22 @@ static void codegen_layout(perm_plan_s &P) {
     partition_alg4(P.L, gr, kCodegenBaseRegs, &k, &c);   // Algorithm 4
     if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
     normalise_split(P.L, &k, &c);
+    P.pure_reg = (P.opts.flags & PERM_FLAG_PURE_REG) != 0;
+    // sum|terms| costs the generated FP64 kernels about a tenth of their speed:
+    // they keep it where precision AUTO may need it (whole walks of n <= 32),
+    // or when asked (PERM_FLAG_ABS_SUM)
+    P.want_abs = P.arith == 0 && ((P.opts.flags & PERM_FLAG_ABS_SUM) ||
+                                  (P.opts.precision == PERM_PREC_AUTO && !P.subrange && n <= kAutoDDMaxN));
+    if (P.pure_reg) {   // CodeGen-PureReg: every row in registers, no chain
+        k = n;
+        c = n - 1;
+    }
     P.k = k;
     P.c = c;
     P.dual = false;
-    if (P.arith == 0) {
+    if (P.pure_reg) {
+        P.ops_per_step = cost_per_step(P.L, true);
+    } else if (P.arith == 0) {
         const double paired = cost_per_step_paired(P.L), dual = cost_per_step_dual(P.L, true);
         P.dual = dual < paired && !(P.opts.flags & PERM_FLAG_PAIRED_CHAIN);
         P.ops_per_step = P.dual ? dual : paired;
@@ -295,18 +381,37 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
     const bool tiny = n <= 8;
     if (engine == PERM_ENGINE_AUTO) engine = (n > 48 || (!tiny && P.len() >= (1ull << 30))) ? PERM_ENGINE_CODEGEN
                                                                                             : PERM_ENGINE_GENERIC;
+    if (P.dd) {   // double-double walks run the precompiled generic kernels only
+        if (n > 48) return fail(PERM_ERR_SIZE, "double-double walks cover n <= 48");
+        engine = PERM_ENGINE_GENERIC;
+    }
     if (engine == PERM_ENGINE_GENERIC && n > 48) return fail(PERM_ERR_SIZE, "generic kernels cover n <= 48");
     const int nmax = nmax_bucket(std::min(n, 48));
-    if (tiny) engine = PERM_ENGINE_GENERIC;
+    if (tiny && engine != PERM_ENGINE_XSHARED) engine = PERM_ENGINE_GENERIC;
+    if (P.dd && engine == PERM_ENGINE_XSHARED) return fail(PERM_ERR_ARG, "the x-in-shared-memory baseline is FP64 only");
     P.engine = engine;
-    P.words = P.arith == 0 ? 2 : P.arith;
+    P.words = result_words(P.arith);
 
-    if (engine == PERM_ENGINE_GENERIC) {
+    if (engine == PERM_ENGINE_XSHARED) {
+        std::vector<unsigned char> img;
+        build_xshared_image(P, img);
+        P.img_bytes = img.size();
+        if ((e = cudaMalloc(&P.d_devmat, img.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(CSC image)");
+        if ((e = cudaMemcpy(P.d_devmat, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpy(CSC image)");
+        cudaFuncAttributes attr;
+        if ((e = xshared_attr(&attr)) != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        P.regs = attr.numRegs;
+        int bps = 0;
+        if ((e = xshared_occupancy(n, (int)P.img_bytes, 256, &bps)) != cudaSuccess) return cuda_fail(e, "occupancy");
+        perm_status_t st = choose_launch(P, 0, std::max(bps, 1), 256);
+        if (st != PERM_OK) return st;
+    } else if (engine == PERM_ENGINE_GENERIC) {
         P.gf = generic_fns(nmax, P.kind());
         if (!P.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this size");
         P.nmax = nmax;
         std::vector<unsigned char> img;
-        build_devmat(P.m, P.L, P.arith, nmax, img);
+        build_devmat(P.m, P.L, P.img_kind(), nmax, img);
         P.img_bytes = img.size();
         if ((e = cudaMalloc(&P.d_devmat, img.size())) != cudaSuccess) return cuda_fail(e, "cudaMalloc(devmat)");
         if ((e = cudaMemcpy(P.d_devmat, img.data(), img.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -349,6 +454,7 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
         bm.chunk_lo = P.chunk_lo;
         bm.chunk_hi = P.chunk_hi;
         bm.K = P.K;
+        bm.abs_shift = P.abs_shift;
         if ((e = cudaMemcpy(P.d_ws + kWsBatchMat, &bm, sizeof(bm), cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpy(batch table)");
     }
@@ -368,8 +474,25 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events) {
     uint64_t *task_out = P.d_ws + kWsTaskOut;
     if (record_events && (e = cudaEventRecord(P.ev0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     if (P.direct) {
-        e = P.gf.direct(P.d_devmat, P.g_lo, P.g_hi, task_out, P.grid, P.block, st);
+        e = P.gf.direct(P.d_devmat, P.g_lo, P.g_hi, task_out, P.grid, P.block, st, P.abs_shift);
         if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+    } else if (P.engine == PERM_ENGINE_XSHARED) {
+        pk::WalkArgs wa;
+        wa.chunk_lo = P.chunk_lo;
+        wa.chunk_hi = P.chunk_hi;
+        wa.ntasks = P.ntasks;
+        wa.task_counter = reinterpret_cast<unsigned long long *>(P.d_ws);
+        wa.task_out = reinterpret_cast<unsigned long long *>(task_out);
+        wa.skip_counter = reinterpret_cast<unsigned long long *>(P.d_ws + 1);
+        wa.K = P.K;
+        wa.zero_skip = 1;
+        wa.timeout_ns = (unsigned long long)std::max(0, P.opts.timeout_ms) * 1000000ull;
+        wa.deadline_word = reinterpret_cast<unsigned long long *>(P.d_ws + kWsDeadline);
+        wa.abort_flag = reinterpret_cast<unsigned int *>(P.d_ws + kWsAbort);
+        e = debug_fail(kSiteLaunch) ? cudaErrorLaunchFailure
+                                    : xshared_launch(wa, P.d_devmat, (int)P.img_bytes, P.m.n, P.abs_shift, P.grid,
+                                                     P.block, st);
+        if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     } else if (P.engine == PERM_ENGINE_GENERIC) {
         pk::BatchArgs ba;
         ba.mats = reinterpret_cast<const pk::BatchMat *>(P.d_ws + kWsBatchMat);
@@ -384,7 +507,7 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events) {
         ba.timeout_ns = (unsigned long long)std::max(0, P.opts.timeout_ms) * 1000000ull;
         ba.deadline_word = reinterpret_cast<unsigned long long *>(P.d_ws + kWsDeadline);
         ba.abort_flag = reinterpret_cast<unsigned int *>(P.d_ws + kWsAbort);
-        e = P.gf.walk(ba, P.grid, P.block, st);
+        e = debug_fail(kSiteLaunch) ? cudaErrorLaunchFailure : P.gf.walk(ba, P.grid, P.block, st);
         if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     } else {
         pk::WalkArgs wa;
@@ -399,7 +522,7 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events) {
         wa.timeout_ns = (unsigned long long)std::max(0, P.opts.timeout_ms) * 1000000ull;
         wa.deadline_word = reinterpret_cast<unsigned long long *>(P.d_ws + kWsDeadline);
         wa.abort_flag = reinterpret_cast<unsigned int *>(P.d_ws + kWsAbort);
-        e = codegen_launch(P, wa, st);
+        e = debug_fail(kSiteLaunch) ? cudaErrorLaunchFailure : codegen_launch(P, wa, st);
         if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     }
     if ((e = reduce_launch(P.arith, task_out, P.ntasks, P.d_ws + 2, st)) != cudaSuccess)
@@ -429,6 +552,7 @@ void describe(const perm_plan_s &P, perm_result_t *out) {
                                ? cost_per_step_dual(P.L, true)
                                : P.ops_per_step;
     out->exact_words = P.m.is_int ? P.arith : 0;
+    out->precision = P.m.is_int ? 0 : (P.dd ? PERM_PREC_DD : PERM_PREC_F64);
 }
 
 // Turns a reduced raw sum (2 words FP64 hi/lo, or w exact words) into the
@@ -437,14 +561,17 @@ perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *r, perm_result_t 
     const int n = P.m.n;
     if (P.zero) { out->status = PERM_OK; return PERM_OK; }
     if (!P.m.is_int) {
-        double hi, lo;
+        double hi, lo, ab;
         std::memcpy(&hi, &r[0], 8);
         std::memcpy(&lo, &r[1], 8);
-        if (P.subrange) { out->f64 = hi; out->f64_lo = lo; }
+        std::memcpy(&ab, &r[2], 8);
+        ab = std::ldexp(ab, P.abs_shift);
+        if (P.subrange) { out->f64 = hi; out->f64_lo = lo; out->abs_term_sum = ab; }
         else {
             const double f = (n % 2) ? 2.0 : -2.0;    // 4 (n mod 2) - 2, Algorithm 1
             out->f64 = hi * f;
             out->f64_lo = lo * f;
+            out->abs_term_sum = 2.0 * ab;
         }
         out->status = PERM_OK;
         return PERM_OK;
@@ -492,10 +619,84 @@ perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out) {
         return fail(PERM_ERR_TIMEOUT, "device-side deadline passed; the walk stopped early");
     }
     const uint64_t skipped = P.h_res[1];
-    const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
-    const uint64_t blocks = (P.g_hi - P.g_lo) >> std::max(1, B);
-    out->zero_skip_frac = (!P.direct && blocks) ? (double)skipped / (double)blocks : 0.0;
+    if (P.engine == PERM_ENGINE_XSHARED) {   // counts skipped steps, not blocks
+        out->zero_skip_frac = (double)skipped / (double)(P.g_hi - P.g_lo);
+    } else {
+        const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
+        const uint64_t blocks = (P.g_hi - P.g_lo) >> std::max(1, B);
+        out->zero_skip_frac = (!P.direct && blocks) ? (double)skipped / (double)blocks : 0.0;
+    }
     return finish_raw(P, P.h_res + 2, out);
+}
+
+static std::atomic<int> g_inject[kSiteCount];
+
+bool debug_fail(int site) {
+    if (site <= 0 || site >= kSiteCount) return false;
+    int v = g_inject[site].load();
+    while (v > 0)
+        if (g_inject[site].compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+bool needs_dd(int n, double perm, double abs_term_sum) {
+    if (!(std::fabs(perm) > 0.0)) return true;   // zero or not a number
+    return (double)n * std::ldexp(1.0, -53) * abs_term_sum > kAutoDDError * std::fabs(perm);
+}
+
+perm_matrix_t matrix_view(const Matrix &m, std::vector<int32_t> &ptr, std::vector<int32_t> &idx,
+                          std::vector<unsigned char> &vals) {
+    const int n = m.n;
+    const size_t vsz = m.is_int ? sizeof(int64_t) : sizeof(double);
+    ptr.assign(n + 1, 0);
+    idx.clear();
+    vals.clear();
+    for (int i = 0; i < n; ++i) {
+        uint64_t cols = m.rowmask[i];
+        while (cols) {
+            const int j = __builtin_ctzll(cols);
+            cols &= cols - 1;
+            idx.push_back(j);
+            const size_t o = vals.size();
+            vals.resize(o + vsz);
+            if (m.is_int) { const int64_t v = m.ival(i, j); std::memcpy(&vals[o], &v, vsz); }
+            else { const double v = m.fval(i, j); std::memcpy(&vals[o], &v, vsz); }
+        }
+        ptr[i + 1] = (int32_t)idx.size();
+    }
+    perm_matrix_t A;
+    A.n = n;
+    A.nnz = (int32_t)idx.size();
+    A.layout = PERM_CSR;
+    A.ptr = ptr.data();
+    A.idx = idx.data();
+    A.vtype = m.is_int ? PERM_I64 : PERM_F64;
+    A.vals = vals.data();
+    return A;
+}
+
+// Precision AUTO: whether a whole FP64 walk of this plan may be rerun in
+// double-double, and the double-double plan of the same matrix.
+static bool auto_dd_eligible(const perm_plan_s &P) {
+    return !P.m.is_int && !P.dd && !P.subrange && !P.zero && P.opts.precision == PERM_PREC_AUTO &&
+           P.m.n <= kAutoDDMaxN;
+}
+
+static perm_status_t make_dd_plan(perm_plan_s &P) {
+    std::vector<int32_t> ptr, idx;
+    std::vector<unsigned char> vals;
+    const perm_matrix_t A = matrix_view(P.m, ptr, idx, vals);
+    perm_opts_t o = P.opts;
+    o.precision = PERM_PREC_DD;
+    o.engine = PERM_ENGINE_GENERIC;
+    o.ordering = P.L.ordering == PERM_ORDER_SEARCH ? PERM_ORDER_AUTO : P.L.ordering;
+    perm_plan_s *D = new (std::nothrow) perm_plan_s();
+    if (!D) return fail(PERM_ERR_NOMEM, "out of host memory");
+    perm_status_t st = plan_prepare(&A, &o, *D);
+    if (st == PERM_OK) st = plan_device_setup(*D);
+    if (st != PERM_OK) { delete D; return st; }
+    P.dd_plan = D;
+    return PERM_OK;
 }
 
 }  // namespace perm
@@ -510,6 +711,7 @@ perm_plan_s::~perm_plan_s() {
     if (graph) cudaGraphExecDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     perm::codegen_release(*this);
+    delete dd_plan;
 }
 
 using namespace perm;
@@ -546,8 +748,30 @@ static bool capture_graph(perm_plan_s &P) {
     return true;
 }
 
+static perm_status_t compute_one(perm_plan_t plan, void *stream, perm_result_t *out);
+
 perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out) {
     if (!plan || !out) return fail(PERM_ERR_ARG, "NULL plan or result");
+    // precision AUTO: a matrix whose FP64 walk proved too ill-conditioned goes
+    // straight to its double-double plan
+    if (plan->dd_plan) {
+        const perm_status_t s = compute_one(plan->dd_plan, stream, out);
+        out->ms_plan = plan->ms_plan + plan->dd_plan->ms_plan;
+        return s;
+    }
+    perm_status_t s = compute_one(plan, stream, out);
+    if (s != PERM_OK || !auto_dd_eligible(*plan) || !needs_dd(plan->m.n, out->f64 + out->f64_lo, out->abs_term_sum))
+        return s;
+    const double ms_fp64 = out->ms_kernel;
+    s = make_dd_plan(*plan);
+    if (s != PERM_OK) { out->status = s; return s; }
+    s = compute_one(plan->dd_plan, stream, out);
+    out->ms_kernel += ms_fp64;
+    out->ms_plan = plan->ms_plan + plan->dd_plan->ms_plan;
+    return s;
+}
+
+static perm_status_t compute_one(perm_plan_t plan, void *stream, perm_result_t *out) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!plan->zero) {
         const bool use_graph = !(plan->opts.flags & PERM_FLAG_NO_GRAPH) && plan->computes >= 1;
@@ -663,6 +887,12 @@ const char *perm_status_string(perm_status_t s) {
 }
 
 const char *perm_last_error(void) { return g_last_error; }
+
+perm_status_t perm_debug_inject_failures(int32_t site, int32_t count) {
+    if (site <= 0 || site >= kSiteCount || count < 0) return fail(PERM_ERR_ARG, "bad injection site or count");
+    g_inject[site].store(count);
+    return PERM_OK;
+}
 
 int32_t perm_device_available(void) {
     int count = 0;

@@ -42,9 +42,10 @@ int BatchGroup::setup(int nmax_, int kind_, int K_target) {
     nmax = nmax_;
     kind = kind_;
     arith = ((kind >> 1) + 1) / 2;
+    img = kind == kKindDD ? kImgDD : (arith ? kImgInt : kImgF64);
     gf = generic_fns(nmax, kind);
     if (!gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this group");
-    words = arith == 0 ? 2 : arith;
+    words = result_words(arith);
     // task table
     mats.resize(plans.size());
     ntasks = 0;
@@ -64,20 +65,21 @@ int BatchGroup::setup(int nmax_, int kind_, int K_target) {
         mats[i].chunk_hi = P.chunk_hi;
         mats[i].out_offset = ntasks;
         mats[i].K = K;
+        mats[i].abs_shift = P.abs_shift;
         ntasks += P.ntasks;
     }
     // images packed back to back (each a multiple of 16 bytes)
     size_t total = 0;
     slot_bytes = 16;
     for (size_t i = 0; i < plans.size(); ++i) {
-        const size_t b = devmat_bytes_for(plans[i]->L, arith, nmax);
+        const size_t b = devmat_bytes_for(plans[i]->L, img, nmax);
         mats[i].image = (int)(total / 16);
         total += b;
         slot_bytes = std::max(slot_bytes, b);
     }
     images.assign(total, 0);
     for (size_t i = 0; i < plans.size(); ++i)
-        build_devmat_into(plans[i]->m, plans[i]->L, arith, nmax, images.data() + (size_t)mats[i].image * 16);
+        build_devmat_into(plans[i]->m, plans[i]->L, img, nmax, images.data() + (size_t)mats[i].image * 16);
     cudaFuncAttributes attr;
     if (gf.attr(&attr) == cudaSuccess) regs = attr.numRegs;
     int bps = 0;
@@ -139,6 +141,93 @@ int BatchGroup::launch(cudaStream_t st, int zero_skip) {
 }  // namespace perm
 
 using namespace perm;
+
+namespace perm {
+
+// Launches every group (one persistent walk and one segmented reduction
+// each, all in one device arena), reads the results back and finishes
+// out[i] for every matrix of the groups.
+static perm_status_t run_groups(std::map<std::pair<int, int>, BatchGroup> &groups, const perm_opts_t &opts,
+                                cudaStream_t st, double ms_plan_each,
+                                std::vector<std::unique_ptr<perm_plan_s>> &plans, perm_result_t *out) {
+    if (groups.empty()) return PERM_OK;
+    size_t total = 0;
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        G.timeout_ns = (unsigned long long)std::max(0, opts.timeout_ms) * 1000000ull;
+        int K_target = opts.chunk_log2;
+        if (!K_target) {
+            if (!chunk_log2_is_tuned(kv.first.first, kv.first.second)) {
+                G.nmax = kv.first.first;
+                G.kind = kv.first.second;
+                G.arith = ((G.kind >> 1) + 1) / 2;
+                G.img = G.kind == kKindDD ? kImgDD : (G.arith ? kImgInt : kImgF64);
+                autotune_group(G, st);
+            }
+            K_target = tuned_chunk_log2(kv.first.first, kv.first.second);
+        }
+        perm_status_t s = (perm_status_t)G.setup(kv.first.first, kv.first.second, K_target);
+        if (s != PERM_OK) return s;
+        total += G.arena_bytes();
+    }
+    DeviceArena arena;
+    cudaError_t e = arena.alloc(total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch arena)");
+    size_t off = 0;
+    for (auto &kv : groups) {
+        kv.second.bind(arena.base + off);
+        off += kv.second.arena_bytes();
+    }
+    EventPair ev;
+    if ((e = ev.create()) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventRecord(ev.e0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (auto &kv : groups) {
+        perm_status_t s = (perm_status_t)kv.second.upload(st);
+        if (s == PERM_OK) s = (perm_status_t)kv.second.launch(st, opts.zero_skip ? 0 : 1);
+        if (s != PERM_OK) return s;
+    }
+    if ((e = cudaEventRecord(ev.e1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    // results back in one copy per group, then the group's counters
+    std::vector<std::vector<uint64_t>> raw;
+    raw.reserve(groups.size());
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        raw.emplace_back(G.mats.size() * (size_t)G.words + 4);
+        if ((e = cudaMemcpyAsync(raw.back().data(), G.d_result, G.mats.size() * (size_t)G.words * 8,
+                                 cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(batch results)");
+        if ((e = cudaMemcpyAsync(raw.back().data() + G.mats.size() * (size_t)G.words, G.d_counters, 32,
+                                 cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(batch counters)");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(batch)");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+    size_t gi = 0;
+    bool timed_out = false;
+    for (auto &kv : groups) {
+        BatchGroup &G = kv.second;
+        const bool aborted = raw[gi][G.mats.size() * (size_t)G.words + 3] != 0;
+        timed_out |= aborted;
+        for (size_t j = 0; j < G.idx.size(); ++j) {
+            const int i = G.idx[j];
+            perm_plan_s &P = *plans[i];
+            P.grid = G.grid;
+            P.block = G.block;
+            P.regs = G.regs;
+            describe(P, &out[i]);
+            out[i].ms_kernel = ms;
+            out[i].ms_plan = ms_plan_each;
+            if (aborted) out[i].status = PERM_ERR_TIMEOUT;
+            else finish_raw(P, raw[gi].data() + j * (size_t)G.words, &out[i]);
+        }
+        ++gi;
+    }
+    if (timed_out) fail(PERM_ERR_TIMEOUT, "device-side deadline passed in a batch walk");
+    return PERM_OK;
+}
+
+}  // namespace perm
 
 extern "C" perm_status_t perm_batch_sequential(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
                                                void *stream, perm_result_t *out) {
@@ -207,92 +296,42 @@ extern "C" perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, co
         groups[{nmax_bucket(P.m.n), P.kind()}].add(i, &P);
     }
     const double t_prep = now_ms() - t0;
-
-    // one arena for every group
     if (opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
-    size_t total = 0;
-    for (auto &kv : groups) {
-        BatchGroup &G = kv.second;
-        G.timeout_ns = (unsigned long long)std::max(0, opts.timeout_ms) * 1000000ull;
-        int K_target = opts.chunk_log2;
-        if (!K_target) {
-            if (!chunk_log2_is_tuned(kv.first.first, kv.first.second)) {
-                G.nmax = kv.first.first;
-                G.kind = kv.first.second;
-                G.arith = ((G.kind >> 1) + 1) / 2;
-                autotune_group(G, st);
-            }
-            K_target = tuned_chunk_log2(kv.first.first, kv.first.second);
-        }
-        perm_status_t s = (perm_status_t)G.setup(kv.first.first, kv.first.second, K_target);
-        if (s != PERM_OK) return s;
-        total += G.arena_bytes();
-    }
-    DeviceArena arena;
-    if (total) {
-        cudaError_t e = arena.alloc(total);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch arena)");
-    }
-    size_t off = 0;
-    for (auto &kv : groups) {
-        kv.second.bind(arena.base + off);
-        off += kv.second.arena_bytes();
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
-    for (auto &kv : groups) {
-        perm_status_t s = (perm_status_t)kv.second.upload(st);
-        if (s == PERM_OK) s = (perm_status_t)kv.second.launch(st, opts.zero_skip ? 0 : 1);
-        if (s != PERM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-    }
-    cudaEventRecord(e1, st);
-    // results back in one copy per group
-    std::vector<std::vector<uint64_t>> raw;
-    raw.reserve(groups.size());
-    for (auto &kv : groups) {
-        BatchGroup &G = kv.second;
-        raw.emplace_back(G.mats.size() * (size_t)G.words + 4);
-        cudaMemcpyAsync(raw.back().data(), G.d_result, G.mats.size() * (size_t)G.words * 8, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(raw.back().data() + G.mats.size() * (size_t)G.words, G.d_counters, 32,
-                        cudaMemcpyDeviceToHost, st);
-    }
-    cudaError_t e = cudaStreamSynchronize(st);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize(batch)");
-    size_t gi = 0;
-    bool timed_out = false;
-    for (auto &kv : groups) {
-        BatchGroup &G = kv.second;
-        const bool aborted = raw[gi][G.mats.size() * (size_t)G.words + 3] != 0;
-        timed_out |= aborted;
-        for (size_t j = 0; j < G.idx.size(); ++j) {
-            const int i = G.idx[j];
+
+    perm_status_t s = run_groups(groups, opts, st, t_prep / count, plans, out);
+    if (s != PERM_OK) return s;
+
+    // precision AUTO: FP64 matrices whose results proved too ill-conditioned
+    // run again, in double-double, as one more launch per NMAX bucket
+    std::map<std::pair<int, int>, BatchGroup> redo;
+    for (auto &kv : groups)
+        for (size_t j = 0; j < kv.second.idx.size(); ++j) {
+            const int i = kv.second.idx[j];
             perm_plan_s &P = *plans[i];
-            P.grid = G.grid;
-            P.block = G.block;
-            P.regs = G.regs;
-            describe(P, &out[i]);
-            out[i].ms_kernel = ms;
-            out[i].ms_plan = t_prep / count;
-            if (aborted) out[i].status = PERM_ERR_TIMEOUT;
-            else finish_raw(P, raw[gi].data() + j * (size_t)G.words, &out[i]);
+            if (!P.m.is_int && !P.dd && opts.precision == PERM_PREC_AUTO && P.m.n <= kAutoDDMaxN &&
+                out[i].status == PERM_OK && needs_dd(P.m.n, out[i].f64 + out[i].f64_lo, out[i].abs_term_sum)) {
+                P.dd = true;
+                redo[{nmax_bucket(P.m.n), P.kind()}].add(i, &P);
+            }
         }
-        ++gi;
+    if (!redo.empty()) {
+        std::vector<double> ms_first(count, 0.0);
+        for (auto &kv : redo)
+            for (int i : kv.second.idx) ms_first[i] = out[i].ms_kernel;
+        s = run_groups(redo, opts, st, t_prep / count, plans, out);
+        if (s != PERM_OK) return s;
+        for (auto &kv : redo)
+            for (int i : kv.second.idx) out[i].ms_kernel += ms_first[i];
     }
-    if (timed_out) fail(PERM_ERR_TIMEOUT, "device-side deadline passed in a batch walk");
+
+    // tiny and very large matrices: their own plans (perm_compute applies AUTO)
     for (int i : singles) {
         perm_plan_s &P = *plans[i];
-        perm_status_t s = plan_device_setup(P);
-        if (s == PERM_OK) s = plan_launch(P, st);
+        s = plan_device_setup(P);
         if (s == PERM_OK) {
-            cudaError_t ce = cudaStreamSynchronize(st);
-            if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamSynchronize");
-            s = plan_finish(P, &out[i]);
+            perm_plan_s *raw = plans[i].release();
+            s = perm_compute(raw, stream, &out[i]);
+            perm_plan_destroy(raw);
         }
         if (s != PERM_OK) { out[i].status = s; if (s == PERM_ERR_CUDA) return s; }
     }

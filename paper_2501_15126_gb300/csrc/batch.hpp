@@ -28,7 +28,8 @@ int autotune_group(const BatchGroup &group, cudaStream_t st);
 struct BatchGroup {
     std::vector<int> idx;                 // positions in the caller's array
     std::vector<perm_plan_s *> plans;
-    int nmax = 0, kind = 0, arith = 0, words = 2;   // kind: generic kernel family (perm_plan_s::kind())
+    int nmax = 0, kind = 0, arith = 0, words = 3;   // kind: generic kernel family (perm_plan_s::kind())
+    int img = 0;                          // image layout (kImgF64, kImgInt, kImgDD)
     GenericFns gf;
     std::vector<pk::BatchMat> mats;
     std::vector<unsigned char> images;
@@ -53,6 +54,19 @@ struct DeviceArena {
     unsigned char *base = nullptr;
     cudaError_t alloc(size_t bytes) { return cudaMalloc(reinterpret_cast<void **>(&base), bytes); }
     ~DeviceArena() { if (base) cudaFree(base); }
+};
+
+// Two timing events destroyed on scope exit.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&e0);
+        return e != cudaSuccess ? e : cudaEventCreate(&e1);
+    }
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
 };
 
 }  // namespace perm

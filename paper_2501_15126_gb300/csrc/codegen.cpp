@@ -98,6 +98,12 @@ int codegen_min_blocks(const perm_plan_s &) {
     }
     return 2;
 }
+// PERM_CODEGEN_NO_FOLD=1: exact kernels multiply every row into the ring on
+// its own (no 32-bit folding), as they did before folding was introduced.
+bool codegen_no_fold() {
+    const char *e = std::getenv("PERM_CODEGEN_NO_FOLD");
+    return e && std::atoi(e) == 1;
+}
 std::string lit(const perm_plan_s &P, double v) {
     char buf[64];
     if (P.arith == 0) {
@@ -151,9 +157,10 @@ struct Emitter {
     // first while the product of the rows' absolute sums (which bound |x_i|
     // at every Gray index) stays below 2^31, then fold each run into the ring
     // with one multiplication.
-    void group_product(int g, const char *ind) {
-        const int b = P.L.group_begin[g], e = P.L.group_begin[g + 1];
-        if (P.arith == 0) {
+    void group_product(int g, const char *ind) { product_range(P.L.group_begin[g], P.L.group_begin[g + 1], ind); }
+    // q *= the slots [b, e), folded in 32 bits on the exact path
+    void product_range(int b, int e, const char *ind) {
+        if (P.arith == 0 || codegen_no_fold()) {
             for (int s = b; s < e; ++s) o << ind << "q = A::mul(q, " << slot(s) << ");\n";
             return;
         }
@@ -270,14 +277,18 @@ struct Emitter {
         else o << "typedef ArithExact<" << P.limbs << "> A;\n";
         o << "struct GenPol {\n";
         o << "    static constexpr int NX = " << std::max(k, 1) << ";\n";
-        o << "    static constexpr bool kPaired = " << (P.arith == 0 ? "true" : "false") << ";\n";
+        o << "    static constexpr bool kPaired = " << (P.arith == 0 && !P.pure_reg ? "true" : "false") << ";\n";
         o << "    static constexpr bool kDual = " << (P.dual ? "true" : "false") << ";\n";
         o << "    static constexpr bool kUnrolledDual = true;\n";
         o << "    typedef A::X X;\n    typedef A::P P;\n";
         o << "    X *xg;\n    unsigned long long stride;\n";
+        // sum|terms| is accumulated as sum|terms| 2^-abs_shift (core.cuh); the
+        // paired step scales its column-0 products by 2^-SH0 and Q_1 by the rest
+        o << "    static constexpr int abs_shift = " << (P.arith == 0 ? P.abs_shift : 0) << ";\n";
+        o << "    static constexpr bool kAbs = " << (P.want_abs ? "true" : "false") << ";\n";
         if (P.dual) {
             for (int g : high_levels2(B)) o << "    P QA" << g << ", QB" << g << ";\n";
-        } else {
+        } else if (!P.pure_reg) {
             for (int g : hi) o << "    P Q" << g << ";\n";
         }
         // flips inside the unrolled block (static column, static or runtime sign)
@@ -310,9 +321,43 @@ struct Emitter {
         // paired steps (FP64): D = prod_{R_0} x - prod_{R_0} (x + S a_0), the
         // column-0 flip applied, Q_1 * D returned.  R_0 = column 0's rows = the
         // first slots.
-        if (P.arith == 0) {
+        // The two terms' magnitudes |Q_1| (|prod_{R_0} x| + |prod_{R_0} (x + S a_0)|)
+        // come back in FP32 through fa: integer and FP32 instructions only.
+        if (P.arith == 0 && P.want_abs) {
             const int r0 = P.L.group_begin[1] - P.L.group_begin[0];
-            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1) {\n";
+            double l0 = 0.0;   // log2 bound of a product over R_0
+            for (int s2 = 0; s2 < r0; ++s2) l0 += std::log2(std::max(row_abs_sum(s2) / 2.0, 1e-300));
+            const int sh0 = (int)std::ceil(l0) - 60;
+            const std::string f1 = "abs_scaled_f32(q1, abs_shift - (" + std::to_string(sh0) + "))";
+            const std::string sh = std::to_string(sh0);
+            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1, float &fa) {\n";
+            if (r0 == 1) {
+                const std::string v = lit(P, value(0, 0));
+                o << "        const X xo = x[0];\n";
+                o << "        if constexpr (S > 0) x[0] += " << v << "; else x[0] -= " << v << ";\n";
+                o << "        fa = " << f1 << " * (abs_scaled_f32(xo, " << sh << ") + abs_scaled_f32(x[0], " << sh
+                  << "));\n";
+                o << "        if constexpr (S > 0) return q1 * -" << v << "; else return q1 * " << v << ";\n";
+            } else {
+                o << "        P px = x[0];\n";
+                for (int s2 = 1; s2 < r0 - 1; ++s2) o << "        px = px * x[" << s2 << "];\n";
+                o << "        const X xl = x[" << r0 - 1 << "];\n";
+                o << "        if constexpr (S > 0) {\n";
+                for (int s2 = 0; s2 < r0; ++s2) o << "            x[" << s2 << "] += " << lit(P, value(0, s2)) << ";\n";
+                o << "        } else {\n";
+                for (int s2 = 0; s2 < r0; ++s2) o << "            x[" << s2 << "] -= " << lit(P, value(0, s2)) << ";\n";
+                o << "        }\n";
+                o << "        P py = x[0];\n";
+                for (int s2 = 1; s2 < r0; ++s2) o << "        py = py * x[" << s2 << "];\n";
+                o << "        fa = " << f1 << " * (abs_scaled_f32(px, " << sh << ") * abs_scaled_f32(xl, 0) + "
+                  << "abs_scaled_f32(py, " << sh << "));\n";
+                o << "        return q1 * fma(px, xl, -py);\n";
+            }
+            o << "    }\n";
+        } else if (P.arith == 0) {   // the same without the magnitudes
+            const int r0 = P.L.group_begin[1] - P.L.group_begin[0];
+            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1, float &fa) {\n";
+            o << "        fa = 0.f;\n";
             if (r0 == 1) {
                 const std::string v = lit(P, value(0, 0));
                 o << "        if constexpr (S > 0) { x[0] += " << v << "; return q1 * -" << v << "; }\n";
@@ -332,16 +377,22 @@ struct Emitter {
             }
             o << "    }\n";
         } else {
-            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1) { return q1; }\n";
+            o << "    template <int S> __device__ __forceinline__ P pair(X (&x)[NX], P q1, float &fa) { fa = 0.f; return q1; }\n";
         }
         // group products of the low levels
         o << "    template <int M> __device__ __forceinline__ P grp(const X (&x)[NX], P q) const {\n";
-        for (int g = 0; g < B; ++g) {
+        if (P.pure_reg) {
+            // the paper's CodeGen-PureReg scheme: the product of all n rows at every step
+            o << "        if constexpr (M == 0) {\n            q = A::one();\n";
+            product_range(0, n, "            ");
+            o << "        }\n        return q;\n    }\n";
+        }
+        for (int g = 0; g < B && !P.pure_reg; ++g) {
             o << "        " << (g ? "else " : "") << "if constexpr (M == " << g << ") {\n";
             if (g < n) group_product(g, "            ");
             o << "        }\n";
         }
-        o << "        return q;\n    }\n";
+        if (!P.pure_reg) o << "        return q;\n    }\n";
         // start vector
         o << "    __device__ __forceinline__ void init_x(X (&x)[NX], unsigned long long G) {\n";
         const int last = P.L.col_order[n - 1];
@@ -376,6 +427,13 @@ struct Emitter {
                 if (P.L.group_begin[h + 1] > P.L.group_begin[h] && h >= B) return "Q" + std::to_string(h);
             return "A::one()";
         };
+        if (P.pure_reg) {   // no chain: every step multiplies all rows
+            o << "    __device__ __forceinline__ P chain_init(const X (&x)[NX]) { return A::one(); }\n";
+            o << "    __device__ __forceinline__ P chain_hi(int j, const X (&x)[NX]) { return A::one(); }\n";
+            o << "};\n}  // namespace pk\n\n";
+            emit_kernel(B);
+            return o.str();
+        }
         o << "    __device__ __forceinline__ P chain_init(const X (&x)[NX]) {\n";
         o << "        P q = A::one();\n";
         for (int g : hi) {
@@ -451,6 +509,7 @@ namespace {
 // Compiles src with NVRTC for sm_103a and loads it into ce.
 perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::string &err) {
     Driver &d = driver();
+    if (debug_fail(kSiteNvrtc)) { err = "NVRTC compile failed (injected by perm_debug_inject_failures)"; return PERM_ERR_NVRTC; }
     nvrtcProgram prog;
     const char *hdr_src[2] = {perm_embedded_core_cuh, perm_embedded_devmat_h};
     const char *hdr_name[2] = {"core.cuh", "devmat.h"};

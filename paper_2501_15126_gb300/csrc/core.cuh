@@ -2,7 +2,8 @@
 //
 // This header is compiled twice: by nvcc into the precompiled generic kernels
 // (generic.cu) and, as source text, by NVRTC into every per-matrix kernel the
-// code generator emits.  It therefore uses no standard headers.
+// code generator emits.  It therefore uses no standard headers.  (The host
+// emulation tests also compile it, with a generated kernel, as host C++.)
 //
 // The walk (Algorithm 1, Nijenhuis-Wilf variant of Eq. 2).  The columns are in
 // the plan's order, column n-1 is never flipped, and x is
@@ -67,10 +68,13 @@ __device__ __forceinline__ u64 warp_or64(u64 v) {
     return ((u64)hi << 32) | lo;
 }
 
-// Nanoseconds from the GPU's global timer.
+// Nanoseconds from the GPU's global timer (0 when the walk code runs as
+// host C++ in the emulation tests).
 __device__ __forceinline__ u64 global_ns() {
-    u64 t;
+    u64 t = 0;
+#ifndef PERM_HOST_EMULATION
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+#endif
     return t;
 }
 
@@ -91,13 +95,32 @@ __device__ __forceinline__ bool past_deadline(u64 timeout_ns, u64 *deadline_word
     return true;
 }
 
+// ------------------------------------------------------------------ sum of |terms|
+// Every FP64 (and double-double) walk also sums the absolute values of its
+// terms, sum_g |prod_i x_i(g)|: the cancellation of the alternating sum
+// (Sec. II) is that sum over |perm|, and it bounds the rounding error of the
+// result.  It is accumulated on the FP32 pipe, so the FP64 pipe that bounds
+// the walk does not see it: |t| 2^-shift is read from the high word of t with
+// integer instructions (the exponent rebiased from 1023 to 127, the top 20
+// fraction bits kept: relative error below 2^-20, always low), then added in
+// FP32.  The per-matrix shift keeps the largest possible term near 2^120;
+// values below 2^-126 after the shift count as zero, from 2^128 on they
+// saturate.
+__device__ __forceinline__ float abs_scaled_f32(double t, int shift) {
+    int h = (__double2hiint(t) & 0x7fffffff) - (896 + shift) * (1 << 20);
+    h = min(max(h, 0), 0x0fefffff);
+    return __int_as_float(h << 3);
+}
+
 // ------------------------------------------------------------------ FP64 arithmetic
 
 struct ArithF64 {
     typedef double X;   // an entry of x
     typedef double P;   // a (partial) product
     typedef double V;   // a matrix value as stored
-    struct Acc { double hi, lo; };
+    typedef double X0;  // a start value as stored
+    // compensated sum (hi, lo) and the sum of |terms| (scaled by 2^-shift)
+    struct Acc { double hi, lo, abs; };
     static constexpr bool kProdIsX = true;   // a product is itself a valid factor
     static __device__ __forceinline__ P one() { return 1.0; }
     static __device__ __forceinline__ P mul(P q, X x) { return q * x; }
@@ -105,19 +128,26 @@ struct ArithF64 {
     static __device__ __forceinline__ bool is_zero(P q) { return q == 0.0; }
     template <int S> static __device__ __forceinline__ X upd(X x, V v) { return S > 0 ? x + v : x - v; }
     static __device__ __forceinline__ X upd_rt(X x, V v, int s) { return fma((double)s, v, x); }
-    // block accumulator: a plain double over 2^B terms
-    typedef double Blk;
-    static __device__ __forceinline__ Blk blk_zero() { return 0.0; }
-    template <int S> static __device__ __forceinline__ void blk_add(Blk &b, P p) { if (S > 0) b += p; else b -= p; }
-    static __device__ __forceinline__ void blk_accumulate(Blk &a, Blk b) { a += b; }
-    static __device__ __forceinline__ Acc acc_zero() { Acc a; a.hi = 0.0; a.lo = 0.0; return a; }
+    static __device__ __forceinline__ X load_x0(const volatile void *base, int i) {
+        return ((const volatile double *)base)[i];
+    }
+    // block accumulator: a plain double over 2^B terms, and their |terms| in FP32
+    struct Blk { double s; float a; };
+    static __device__ __forceinline__ Blk blk_zero() { Blk b; b.s = 0.0; b.a = 0.f; return b; }
+    template <int S> static __device__ __forceinline__ void blk_add(Blk &b, P p) { if (S > 0) b.s += p; else b.s -= p; }
+    // |t| of one term, and an already scaled FP32 contribution
+    static __device__ __forceinline__ void blk_abs(Blk &b, P t, int shift) { b.a += abs_scaled_f32(t, shift); }
+    static __device__ __forceinline__ void blk_abs_f(Blk &b, float f) { b.a += f; }
+    static __device__ __forceinline__ void blk_accumulate(Blk &a, Blk b) { a.s += b.s; a.a += b.a; }
+    static __device__ __forceinline__ Acc acc_zero() { Acc a; a.hi = 0.0; a.lo = 0.0; a.abs = 0.0; return a; }
     // TwoSum (Knuth): a.hi + b = s + e exactly
     static __device__ __forceinline__ void acc_merge(Acc &a, Blk b) {
-        double s = a.hi + b;
+        double s = a.hi + b.s;
         double bb = s - a.hi;
-        double e = (a.hi - (s - bb)) + (b - bb);
+        double e = (a.hi - (s - bb)) + (b.s - bb);
         a.hi = s;
         a.lo += e;
+        a.abs += (double)b.a;
     }
     static __device__ __forceinline__ Acc acc_add(Acc a, Acc b) {
         double s = a.hi + b.hi;
@@ -127,25 +157,111 @@ struct ArithF64 {
         Acc r;
         r.hi = s + e;
         r.lo = e - (r.hi - s);
+        r.abs = a.abs + b.abs;
         return r;
     }
     static __device__ __forceinline__ Acc shfl_down(Acc a, int d) {
         Acc r;
         r.hi = __shfl_down_sync(PERM_FULLMASK, a.hi, d);
         r.lo = __shfl_down_sync(PERM_FULLMASK, a.lo, d);
+        r.abs = __shfl_down_sync(PERM_FULLMASK, a.abs, d);
         return r;
     }
-    static constexpr int ACC_WORDS = 2;   // stored as two doubles
+    static constexpr int ACC_WORDS = 3;   // stored as three doubles
     static __device__ __forceinline__ void acc_store(u64 *dst, Acc a) {
         dst[0] = (u64)__double_as_longlong(a.hi);
         dst[1] = (u64)__double_as_longlong(a.lo);
+        dst[2] = (u64)__double_as_longlong(a.abs);
     }
     static __device__ __forceinline__ Acc acc_load(const u64 *src) {
         Acc a;
         a.hi = __longlong_as_double((long long)src[0]);
         a.lo = __longlong_as_double((long long)src[1]);
+        a.abs = __longlong_as_double((long long)src[2]);
         return a;
     }
+};
+
+// ------------------------------------------------------------------ double-double arithmetic
+// For ill-conditioned FP64 inputs (sum|terms| / |perm| large): every x_i,
+// product and sum is an unevaluated pair of doubles h + l (about 106 bits).
+// x updates are exact TwoSum additions (Knuth), products are FMA-based exact
+// products of the high parts (Dekker's two-product, done with one fused
+// multiply-add) plus the cross terms, so a term carries a relative error of a
+// few 2^-104 instead of n 2^-53.  Same walk, same terms; only the precision of
+// each operation changes.  The results use the FP64 accumulator and reduction.
+
+struct DD { double h, l; };
+
+struct ArithDD {
+    typedef DD X;
+    typedef DD P;
+    typedef double V;
+    typedef DD X0;
+    typedef ArithF64::Acc Acc;
+    static constexpr bool kProdIsX = true;
+    static __device__ __forceinline__ DD mk(double h, double l) { DD r; r.h = h; r.l = l; return r; }
+    static __device__ __forceinline__ P one() { return mk(1.0, 0.0); }
+    // (q.h + q.l)(x.h + x.l) ~ p + e: p = q.h x.h rounded, e = its exact error
+    // (one FMA) plus the cross terms; q.l x.l (below 2^-104 relative) dropped
+    static __device__ __forceinline__ P mul(P q, X x) {
+        const double p = q.h * x.h;
+        double e = fma(q.h, x.h, -p);
+        e = fma(q.h, x.l, e);
+        e = fma(q.l, x.h, e);
+        return mk(p, e);
+    }
+    // (a.h + a.l) + b, renormalised so that |l| <= ulp(h)/2
+    static __device__ __forceinline__ DD add_d(DD a, double b) {
+        const double s = a.h + b;
+        const double bb = s - a.h;
+        const double e = (a.h - (s - bb)) + (b - bb);
+        const double l = a.l + e;
+        const double h = s + l;
+        return mk(h, l - (h - s));
+    }
+    static __device__ __forceinline__ DD add_dd(DD a, DD b) {
+        const double s = a.h + b.h;
+        const double bb = s - a.h;
+        double e = (a.h - (s - bb)) + (b.h - bb);
+        e += a.l + b.l;
+        const double h = s + e;
+        return mk(h, e - (h - s));
+    }
+    static __device__ __forceinline__ double neg_if(double v, int s) {
+        return s < 0 ? __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v)) : v;
+    }
+    static __device__ __forceinline__ P diff(P a, P b) { return add_dd(a, mk(-b.h, -b.l)); }
+    static __device__ __forceinline__ bool is_zero(P q) { return q.h == 0.0 && q.l == 0.0; }
+    template <int S> static __device__ __forceinline__ X upd(X x, V v) { return add_d(x, S > 0 ? v : -v); }
+    // s is +1, -1 or 0 (the start vector adds a column with weight 0 or 1)
+    static __device__ __forceinline__ X upd_rt(X x, V v, int s) { return s == 0 ? x : add_d(x, neg_if(v, s)); }
+    static __device__ __forceinline__ X load_x0(const volatile void *base, int i) {
+        const volatile double *d = (const volatile double *)base;
+        return mk(d[2 * i], d[2 * i + 1]);
+    }
+    struct Blk { DD s; float a; };
+    static __device__ __forceinline__ Blk blk_zero() { Blk b; b.s = mk(0.0, 0.0); b.a = 0.f; return b; }
+    template <int S> static __device__ __forceinline__ void blk_add(Blk &b, P p) {
+        b.s = add_dd(b.s, S > 0 ? p : mk(-p.h, -p.l));
+    }
+    static __device__ __forceinline__ void blk_abs(Blk &b, P t, int shift) { b.a += abs_scaled_f32(t.h, shift); }
+    static __device__ __forceinline__ void blk_abs_f(Blk &b, float f) { b.a += f; }
+    static __device__ __forceinline__ void blk_accumulate(Blk &a, Blk b) { a.s = add_dd(a.s, b.s); a.a += b.a; }
+    static __device__ __forceinline__ Acc acc_zero() { return ArithF64::acc_zero(); }
+    static __device__ __forceinline__ void acc_merge(Acc &a, Blk b) {
+        double s = a.hi + b.s.h;
+        double bb = s - a.hi;
+        double e = (a.hi - (s - bb)) + (b.s.h - bb);
+        a.hi = s;
+        a.lo += e + b.s.l;
+        a.abs += (double)b.a;
+    }
+    static __device__ __forceinline__ Acc acc_add(Acc a, Acc b) { return ArithF64::acc_add(a, b); }
+    static __device__ __forceinline__ Acc shfl_down(Acc a, int d) { return ArithF64::shfl_down(a, d); }
+    static constexpr int ACC_WORDS = ArithF64::ACC_WORDS;
+    static __device__ __forceinline__ void acc_store(u64 *dst, Acc a) { ArithF64::acc_store(dst, a); }
+    static __device__ __forceinline__ Acc acc_load(const u64 *src) { return ArithF64::acc_load(src); }
 };
 
 // ------------------------------------------------------------------ exact arithmetic
@@ -235,8 +351,12 @@ struct ArithExact {
     typedef int X;
     typedef Ring<L> P;
     typedef int V;
+    typedef int X0;
     typedef Ring<L> Acc;
     typedef Ring<L> Blk;
+    static __device__ __forceinline__ X load_x0(const volatile void *base, int i) { return ((const volatile int *)base)[i]; }
+    static __device__ __forceinline__ void blk_abs(Blk &, const P &, int) {}
+    static __device__ __forceinline__ void blk_abs_f(Blk &, float) {}
     static __device__ __forceinline__ P one() {
         P r;
 #pragma unroll
@@ -293,6 +413,12 @@ struct ArithExact {
     }
 };
 
+// Adds |t| of one term to the block's sum of |terms|, if the policy keeps it.
+template <class Pol, class A>
+__device__ __forceinline__ void term_abs(const Pol &pol, typename A::Blk &blk, const typename A::P &t) {
+    if constexpr (Pol::kAbs) A::blk_abs(blk, t, pol.abs_shift);
+}
+
 // ------------------------------------------------------------------ the unrolled block
 // Step l (1 <= l < 2^B) of a block flips column J = ctz(l).  Its sign is bit
 // J+1 of l for J < B-1; for J = B-1 it is bit B of the block start, passed in
@@ -328,6 +454,7 @@ struct BlockSteps {
             LevelsDown<Pol, A, Bv, J>::run(pol, x, Q);
             typename A::P p = pol.template grp<0>(x, Q[1]);
             A::template blk_add<(Lstep & 1) ? -1 : 1>(blk, p);
+            term_abs<Pol, A>(pol, blk, p);
             BlockSteps<Pol, A, Bv, Lstep + 1>::run(pol, x, Q, blk, s_mid);
         }
     }
@@ -339,7 +466,8 @@ struct BlockSteps {
 // exactly column 0's rows, so their two terms combine into
 //   (-1)^l (P(l) - P(l+1)) = Q_1 (prod_{R_0} x - prod_{R_0} (x + s a_0)),
 // formed once by the policy's pair<s>() (which also applies the column-0
-// flip).  Same terms, about 1.5 fewer multiply/add operations per step.
+// flip, and returns |P(l)| + |P(l+1)|, scaled, in FP32 through its last
+// argument).  Same terms, about 1.5 fewer multiply/add operations per step.
 template <class Pol, class A, int Bv, int Lstep>
 struct PairSteps {
     static __device__ __forceinline__ void run(Pol &pol, typename A::X (&x)[Pol::NX], typename A::P (&Q)[Bv + 1],
@@ -354,7 +482,9 @@ struct PairSteps {
             }
             LevelsDown<Pol, A, Bv, J>::run(pol, x, Q);
             constexpr int S0 = (((Lstep + 1) >> 1) & 1) ? -1 : 1;
-            A::template blk_add<1>(blk, pol.template pair<S0>(x, Q[1]));
+            float fa;
+            A::template blk_add<1>(blk, pol.template pair<S0>(x, Q[1], fa));
+            if constexpr (Pol::kAbs) A::blk_abs_f(blk, fa);
             PairSteps<Pol, A, Bv, Lstep + 2>::run(pol, x, Q, blk, s_mid);
         }
     }
@@ -389,9 +519,13 @@ __device__ __forceinline__ void dual_block(Pol &pol, typename A::X (&x)[Pol::NX]
                 if (M <= j) pol.level2(M, x, QA[M + 1], QB[M + 1], QA[M], QB[M]);
         }
         A::template blk_add<1>(blk, A::diff(QA[1], QB[1]));
+        term_abs<Pol, A>(pol, blk, QA[1]);
+        term_abs<Pol, A>(pol, blk, QB[1]);
         pol.flip_dyn(1, x, (p2 & 1) ? -1 : 1);
         pol.level2(1, x, QA[2], QB[2], QA[1], QB[1]);
         A::template blk_add<-1>(blk, A::diff(QA[1], QB[1]));
+        term_abs<Pol, A>(pol, blk, QA[1]);
+        term_abs<Pol, A>(pol, blk, QB[1]);
     }
 }
 
@@ -424,6 +558,8 @@ struct DualSteps {
                 LevelsDown2<Pol, A, Bv, J>::run(pol, x, QA, QB);
             }
             A::template blk_add<(Pp & 1) ? -1 : 1>(blk, A::diff(QA[1], QB[1]));
+            term_abs<Pol, A>(pol, blk, QA[1]);
+            term_abs<Pol, A>(pol, blk, QB[1]);
             DualSteps<Pol, A, Bv, Pp + 1>::run(pol, x, QA, QB, blk, s_mid);
         }
     }
@@ -519,10 +655,14 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
         typename A::Blk blk = A::blk_zero();
         if constexpr (Pol::kPaired) {
             // steps 0 and 1 (column 0, sign +: bit 1 of 1 is 0), then pairs (2,3), (4,5), ...
-            A::template blk_add<1>(blk, pol.template pair<1>(x, Q[1]));
+            float fa;
+            A::template blk_add<1>(blk, pol.template pair<1>(x, Q[1], fa));
+            if constexpr (Pol::kAbs) A::blk_abs_f(blk, fa);
             PairSteps<Pol, A, Bv, 2>::run(pol, x, Q, blk, s_mid);
         } else {
-            A::template blk_add<1>(blk, pol.template grp<0>(x, Q[1]));
+            const typename A::P p0 = pol.template grp<0>(x, Q[1]);
+            A::template blk_add<1>(blk, p0);
+            term_abs<Pol, A>(pol, blk, p0);
             BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
         }
         A::blk_accumulate(mid, blk);

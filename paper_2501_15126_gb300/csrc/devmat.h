@@ -34,6 +34,8 @@ struct BatchMat {
     unsigned long long out_offset;
     int image;
     int K;
+    int abs_shift;                      // FP64 / double-double: sum|terms| is kept as sum|terms| 2^-abs_shift
+    int reserved;
 };
 
 // Launch arguments of the generic kernels: any number of matrices of one
@@ -63,8 +65,10 @@ struct BatchArgs {
 // Group 0 is sorted by the next column that touches each of its rows: S_m,
 // the rows of column 0 next touched by column m, are the contiguous slots
 // [sbegin[m], sbegin[m+1]).  For NMAX in {16, 32, 48} the header is
-// 48 + 12 NMAX bytes, a multiple of 16.
-template <int NMAX, typename V>
+// 48 + 12 NMAX bytes, a multiple of 16.  X0 is the type of the start values:
+// V itself, except on the double-double path, whose start values are exact
+// pairs of doubles (hi, lo) while the matrix values stay doubles.
+template <int NMAX, typename V, typename X0 = V>
 struct DevMat {
     int n;                              // dimension
     int top;                            // highest m with group m or S_m nonempty
@@ -74,7 +78,7 @@ struct DevMat {
     unsigned short colptr[NMAX];        // first value of column p
     unsigned char gbegin[NMAX + 16];    // first slot of group m (m <= n; gbegin[n] = n)
     unsigned char sbegin[NMAX + 16];    // first slot of S_m (1 <= m <= n; sbegin[n] = |group 0|)
-    V x0[NMAX];                         // Nijenhuis-Wilf start values by slot
+    X0 x0[NMAX];                        // Nijenhuis-Wilf start values by slot
     V val[NMAX * NMAX];                 // nnz values, column after column
 };
 

@@ -81,6 +81,7 @@ cudaError_t batch_reduce_launch(int arith, const pk::BatchMat *mats, int nmat, u
 }
 
 GenericFns generic_fns_f64(int nmax);
+GenericFns generic_fns_dd(int nmax);
 GenericFns generic_fns_r64(int nmax, int fold);
 GenericFns generic_fns_r96(int nmax, int fold);
 GenericFns generic_fns_r128(int nmax, int fold);
@@ -90,7 +91,7 @@ GenericFns generic_fns_r192(int nmax, int fold);
 GenericFns generic_fns(int nmax, int kind) {
     const int limbs = kind >> 1, fold = kind & 1;
     switch (limbs) {
-    case 0: return fold ? GenericFns() : generic_fns_f64(nmax);
+    case 0: return fold ? generic_fns_dd(nmax) : generic_fns_f64(nmax);
     case 2: return generic_fns_r64(nmax, fold);
     case 3: return generic_fns_r96(nmax, fold);
     case 4: return generic_fns_r128(nmax, fold);

@@ -76,17 +76,19 @@ struct GenericPol {
     // chain's registers would spill x, so that bucket keeps one chain too.
     static constexpr bool kDual = A::kProdIsX && NMAX <= 32;
     static constexpr bool kUnrolledDual = false;   // the pairs of a block are a rolled loop
+    static constexpr bool kAbs = true;             // sum|terms| is always kept
     typedef typename A::X X;
     typedef typename A::P P;
     typedef typename A::V V;
-    typedef DevMat<NMAX, V> M;
+    typedef DevMat<NMAX, V, typename A::X0> M;
     typedef typename SlotMask<NMAX>::T Mask;
 
     const M *m;
+    int abs_shift;      // sum|terms| is accumulated as sum|terms| 2^-abs_shift
     P Qh[NMAX + 1];     // chain levels >= B (dynamic index: local memory)
     P Bh[kDual ? NMAX + 1 : 1];   // the same levels of the column-0-on chain
 
-    __device__ __forceinline__ explicit GenericPol(const M *mat) : m(mat) {}
+    __device__ __forceinline__ GenericPol(const M *mat, int shift) : m(mat), abs_shift(shift) {}
 
     __device__ __forceinline__ int gbegin(int g) const { return ((const volatile unsigned char *)m->gbegin)[g]; }
     __device__ __forceinline__ int sbegin(int g) const { return ((const volatile unsigned char *)m->sbegin)[g]; }
@@ -263,6 +265,8 @@ struct GenericPol {
         }
         A::template blk_add<1>(blk, p0);
         A::template blk_add<-1>(blk, p1);
+        A::blk_abs(blk, p0, abs_shift);
+        A::blk_abs(blk, p1, abs_shift);
     }
     // levels from..to of the single chain (Qh, local memory), from >= to,
     // each from the one above; returns level `to`
@@ -342,7 +346,7 @@ struct GenericPol {
     // called by the whole warp, which visits the union of its lanes' columns
     __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
 #pragma unroll
-        for (int i = 0; i < NMAX; ++i) x[i] = ((const volatile V *)m->x0)[i];
+        for (int i = 0; i < NMAX; ++i) x[i] = A::load_x0(m->x0, i);
         u64 U = warp_or64(G);
         while (U) {
             const int p = ctz64(U);
@@ -422,7 +426,7 @@ __device__ __forceinline__ typename A::Acc walk_chunk_compact(GenericPol<NMAX, A
 // only when the matrix changes).
 template <int NMAX, class A>
 __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned char *slot_raw) {
-    typedef DevMat<NMAX, typename A::V> M;
+    typedef DevMat<NMAX, typename A::V, typename A::X0> M;
     const int lane = threadIdx.x & 31;
     M *slot = reinterpret_cast<M *>(slot_raw);
     int cached = -1;
@@ -456,7 +460,7 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
         u64 q = bm.chunk_lo + (task - bm.task_begin) * 32ull + (u64)lane;
         const bool live = q < bm.chunk_hi;
         if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
-        GenericPol<NMAX, A> pol(slot);
+        GenericPol<NMAX, A> pol(slot, bm.abs_shift);
         typename A::Acc acc;
         if constexpr (GenericPol<NMAX, A>::kDual)
             acc = walk_chunk_dual<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
@@ -476,9 +480,15 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
 template <class A> struct LimbsOf { static constexpr int v = 0; };
 template <int NL> struct LimbsOf<ArithExact<NL>> { static constexpr int v = NL; };
 template <int NL> struct LimbsOf<ArithExactFold<NL>> { static constexpr int v = NL; };
+// Double-double walks hold two doubles per slot and get the whole register
+// file of one block.
+template <class A> struct IsDD { static constexpr bool v = false; };
+template <> struct IsDD<ArithDD> { static constexpr bool v = true; };
 template <int NMAX, class A> struct WalkMinBlocks {
     static constexpr int L = LimbsOf<A>::v;
-    static constexpr int v = (L > 0 && ((NMAX == 16 && L <= 5) || (NMAX == 32 && L <= 3))) ? 3 : PERM_GENERIC_MIN_BLOCKS;
+    static constexpr int v = IsDD<A>::v ? 1
+                             : (L > 0 && ((NMAX == 16 && L <= 5) || (NMAX == 32 && L <= 3))) ? 3
+                                                                                             : PERM_GENERIC_MIN_BLOCKS;
 };
 
 template <int NMAX, class A>
@@ -490,15 +500,15 @@ __global__ void __launch_bounds__(256, WalkMinBlocks<NMAX, A>::v) k_walk_generic
 
 // Tiny matrices: one thread per Gray index, x built from scratch.
 template <int NMAX, class A>
-__global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typename A::V> *m, u64 g_lo, u64 g_hi,
-                                                        u64 *block_out) {
+__global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typename A::V, typename A::X0> *m, u64 g_lo,
+                                                        u64 g_hi, u64 *block_out, int abs_shift) {
     typedef typename A::X X;
     const u64 g = g_lo + (u64)blockIdx.x * blockDim.x + threadIdx.x;
     typename A::Acc acc = A::acc_zero();
     if (g < g_hi) {
         X x[NMAX];
 #pragma unroll
-        for (int i = 0; i < NMAX; ++i) x[i] = m->x0[i];
+        for (int i = 0; i < NMAX; ++i) x[i] = A::load_x0(m->x0, i);
         u64 G = g ^ (g >> 1);
         while (G) {
             const int p = ctz64(G);
@@ -515,6 +525,7 @@ __global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typen
             if (i < m->n) q = A::mul(q, x[i]);
         typename A::Blk b = A::blk_zero();
         if (g & 1ull) A::template blk_add<-1>(b, q); else A::template blk_add<1>(b, q);
+        A::blk_abs(b, q, abs_shift);
         A::acc_merge(acc, b);
     }
 #pragma unroll
@@ -548,10 +559,10 @@ static cudaError_t launch_walk_t(const pk::BatchArgs &ba, int grid, int block, c
 
 template <int NMAX, class A>
 static cudaError_t launch_direct_t(const void *devmat, uint64_t g_lo, uint64_t g_hi, uint64_t *out, int grid,
-                                   int block, cudaStream_t st) {
+                                   int block, cudaStream_t st, int abs_shift) {
     pk::k_direct_generic<NMAX, A><<<grid, block, 0, st>>>(
-        reinterpret_cast<const pk::DevMat<NMAX, typename A::V> *>(devmat), g_lo, g_hi,
-        reinterpret_cast<unsigned long long *>(out));
+        reinterpret_cast<const pk::DevMat<NMAX, typename A::V, typename A::X0> *>(devmat), g_lo, g_hi,
+        reinterpret_cast<unsigned long long *>(out), abs_shift);
     return cudaGetLastError();
 }
 
@@ -577,7 +588,7 @@ static GenericFns make_fns() {
     f.attr = attr_walk_t<NMAX, A>;
     f.occ = occ_walk_t<NMAX, A>;
     f.block_log2 = PERM_GENERIC_B;
-    f.devmat_bytes = sizeof(pk::DevMat<NMAX, typename A::V>);   // capacity of a dense image
+    f.devmat_bytes = sizeof(pk::DevMat<NMAX, typename A::V, typename A::X0>);   // capacity of a dense image
     return f;
 }
 

@@ -447,6 +447,17 @@ double bound_log2(const Matrix &m) {
     return std::min(rows, cols);
 }
 
+int abs_shift_for(const Matrix &m) {
+    double L = 0.0;
+    for (int i = 0; i < m.n; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < m.n; ++j) rs += std::fabs(m.fval(i, j));
+        if (rs > 0.0) L += std::log2(rs / 2.0);
+    }
+    const double s = std::ceil(L) - 120.0;
+    return (int)std::min(1100.0, std::max(-890.0, s));
+}
+
 int exact_words_for(double bound, int n) {
     if (!(bound < 125.0)) return 0;               // result must fit a signed 128-bit integer
     for (int w = 1; w <= 3; ++w)

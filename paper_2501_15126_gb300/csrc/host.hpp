@@ -100,6 +100,12 @@ int64_t threads_for_regs(int regs);
 // otherwise min over rows/cols of prod of absolute sums.  -inf for zero rows.
 double bound_log2(const Matrix &m);
 
+// The scale of the FP64 walks' sum of |terms|: every |x_i(g)| is at most half
+// row i's absolute sum, so every term is at most 2^L, L = sum_i log2(r_i / 2);
+// the kernels accumulate sum|terms| 2^-shift with shift = ceil(L) - 120
+// (clamped to the range the FP32 accumulation can take).
+int abs_shift_for(const Matrix &m);
+
 // Smallest w in 1..3 with the doubled-NW sum recoverable modulo 2^(64 w),
 // or 0 when even w = 3 is not enough.
 int exact_words_for(double bound, int n);

@@ -47,62 +47,7 @@ __global__ void __launch_bounds__(256) k_imad_rate(unsigned *out, int iters, uns
     out[t] = s;
 }
 
-// The same chains with every DFMA guarded by a predicate taken from a kernel
-// argument: does a false predicate save FP64 pipe time?
-__global__ void __launch_bounds__(256) k_fp64_pred(double *out, int iters, double b, double c, int on) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double a0 = 1 + t, a1 = 2 + t, a2 = 3 + t, a3 = 4 + t, a4 = 5 + t, a5 = 6 + t, a6 = 7 + t, a7 = 8 + t;
-    for (int it = 0; it < iters; ++it) {
-#pragma unroll
-        for (int r = 0; r < kUnroll; ++r) {
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.s32 p, %9, 0;\n"
-                "@p fma.rn.f64 %0, %0, %8, %10;\n @p fma.rn.f64 %1, %1, %8, %10;\n"
-                "@p fma.rn.f64 %2, %2, %8, %10;\n @p fma.rn.f64 %3, %3, %8, %10;\n"
-                "@p fma.rn.f64 %4, %4, %8, %10;\n @p fma.rn.f64 %5, %5, %8, %10;\n"
-                "@p fma.rn.f64 %6, %6, %8, %10;\n @p fma.rn.f64 %7, %7, %8, %10;\n}"
-                : "+d"(a0), "+d"(a1), "+d"(a2), "+d"(a3), "+d"(a4), "+d"(a5), "+d"(a6), "+d"(a7)
-                : "d"(b), "r"(on), "d"(c));
-        }
-    }
-    out[t] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
-}
-
 }  // namespace
-
-extern "C" perm_status_t perm_fp64_predication_rates(void *stream, double *issued_on, double *issued_off) {
-    if (!issued_on || !issued_off) return perm::fail(PERM_ERR_ARG, "NULL output");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return perm::cuda_fail(e, "device query");
-    const int block = 256, grid = sms * 8, iters = 400;
-    void *buf = nullptr;
-    if ((e = cudaMalloc(&buf, (size_t)grid * block * sizeof(double))) != cudaSuccess) return perm::cuda_fail(e, "cudaMalloc");
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    double rate[2] = {0.0, 0.0};
-    for (int on = 1; on >= 0; --on) {
-        k_fp64_pred<<<grid, block, 0, st>>>((double *)buf, 4, 0.999, 1e-7, on);
-        cudaEventRecord(e0, st);
-        k_fp64_pred<<<grid, block, 0, st>>>((double *)buf, iters, 0.999, 1e-7, on);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        rate[on] = (double)grid * block * iters * kUnroll * 8 / (ms * 1e-3);
-    }
-    e = cudaGetLastError();
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(buf);
-    if (e != cudaSuccess) return perm::cuda_fail(e, "predication probe");
-    *issued_on = rate[1];
-    *issued_off = rate[0];
-    return PERM_OK;
-}
 
 extern "C" perm_status_t perm_issue_rates(void *stream, double *fp64_ops_per_s, double *imad_ops_per_s) {
     if (!fp64_ops_per_s || !imad_ops_per_s) return perm::fail(PERM_ERR_ARG, "NULL output");

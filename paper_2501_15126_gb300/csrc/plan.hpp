@@ -11,6 +11,32 @@
 #include "host.hpp"
 #include "kernels.hpp"
 
+namespace perm {
+
+// Layouts of the matrix image (devmat.h): FP64 values and start values,
+// doubled int32 values and start values, or FP64 values with exact
+// double-double start values.
+constexpr int kImgF64 = 0, kImgInt = 1, kImgDD = 2;
+
+// 64-bit words of one task result: the FP64 accumulator (hi, lo, sum|terms|)
+// or the exact ring's words.
+inline int result_words(int arith) { return arith == 0 ? 3 : arith; }
+
+// Precision AUTO reruns an FP64 walk in double-double arithmetic when its
+// rounding-error estimate n 2^-53 sum|terms| / |perm| exceeds this (a factor
+// of 10 below the 1e-9 relative target), for walks of at most 2^31 steps.
+constexpr double kAutoDDError = 1e-10;
+constexpr int kAutoDDMaxN = 32;
+bool needs_dd(int n, double perm, double abs_term_sum);
+
+// Host-side failure injection for tests (perm_debug_inject_failures): each
+// call consumes one pending injected failure of `site`, if any, and the
+// caller then behaves as if the call made there had failed.
+enum { kSiteWaveLaunch = 1, kSiteNvrtc = 2, kSiteFinish = 3, kSiteUpload = 4, kSiteLaunch = 5, kSiteCount = 6 };
+bool debug_fail(int site);
+
+}  // namespace perm
+
 struct perm_plan_s {
     perm::Matrix m;
     perm::Layout L;
@@ -19,7 +45,12 @@ struct perm_plan_s {
     int limbs = 0;            // 0 = FP64, else the walk's ring Z/2^(32 limbs): 2 arith - 1 or 2 arith
     bool fold = false;        // exact: every row's absolute sum <= 127 (folded products)
     bool dual = false;        // generated FP64 kernel with two-state chains (cheaper than pairing)
-    int kind() const { return 2 * limbs + (fold ? 1 : 0); }   // generic kernel family
+    bool dd = false;          // FP64 input walked in double-double arithmetic
+    bool pure_reg = false;    // codegen: a full product of all n rows every step (CodeGen-PureReg)
+    bool want_abs = true;     // FP64 walks: accumulate sum|terms| (generated kernels: see codegen_layout)
+    int abs_shift = 0;        // FP64 / double-double: sum|terms| is accumulated as sum|terms| 2^-abs_shift
+    int kind() const { return dd ? perm::kKindDD : 2 * limbs + (fold ? 1 : 0); }   // generic kernel family
+    int img_kind() const { return dd ? perm::kImgDD : (arith ? perm::kImgInt : perm::kImgF64); }   // matrix image layout
     uint64_t total = 0;       // 2^(n-1)
     uint64_t g_lo = 0, g_hi = 0;
     bool subrange = false;
@@ -44,6 +75,10 @@ struct perm_plan_s {
     cudaStream_t cap_stream = nullptr;     // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;       // the captured launches (second call on)
     bool graph_failed = false;
+    // precision AUTO: the double-double plan of this matrix, made when a
+    // compute's FP64 result proved too ill-conditioned; later computes use it
+    // directly
+    perm_plan_s *dd_plan = nullptr;
     uint64_t len() const { return g_hi - g_lo; }
     ~perm_plan_s();
 };
@@ -51,7 +86,7 @@ struct perm_plan_s {
 namespace perm {
 
 // Workspace layout (64-bit words): [0] task counter, [1] skipped blocks,
-// [2..4] reduced result, [5] deadline, [6] abort flag, [8..12] the
+// [2..4] reduced result, [5] deadline, [6] abort flag, [8..13] the
 // single-matrix BatchMat, [16..] task results.  Words 0..7 are cleared
 // before every launch.
 constexpr size_t kWsDeadline = 5;
@@ -74,10 +109,14 @@ perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out);
 void describe(const perm_plan_s &P, perm_result_t *out);
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);
 int nmax_bucket(int n);
-void build_devmat(const Matrix &m, const Layout &L, int arith, int nmax, std::vector<unsigned char> &img);
-size_t devmat_bytes(int arith, int nmax, int nnz);
-size_t devmat_bytes_for(const Layout &L, int arith, int nmax);
-void build_devmat_into(const Matrix &m, const Layout &L, int arith, int nmax, unsigned char *dst);
+// Matrix images; img is kImgF64, kImgInt or kImgDD.
+void build_devmat(const Matrix &m, const Layout &L, int img, int nmax, std::vector<unsigned char> &img_out);
+size_t devmat_bytes(int img, int nmax, int nnz);
+size_t devmat_bytes_for(const Layout &L, int img, int nmax);
+void build_devmat_into(const Matrix &m, const Layout &L, int img, int nmax, unsigned char *dst);
+// A CSR view of a prepared matrix (for re-planning it), backed by the vectors.
+perm_matrix_t matrix_view(const Matrix &m, std::vector<int32_t> &ptr, std::vector<int32_t> &idx,
+                          std::vector<unsigned char> &vals);
 perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, int block);
 
 }  // namespace perm

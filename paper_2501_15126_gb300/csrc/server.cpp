@@ -101,7 +101,8 @@ struct RangeAlloc {
 };
 
 struct Family {
-    int nmax = 0, kind = 0, arith = 0, words = 2, K_target = 14;   // kind: generic kernel family
+    int nmax = 0, kind = 0, arith = 0, words = 3, K_target = 14;   // kind: generic kernel family
+    int img = 0;                                                  // image layout (kImgF64, kImgInt, kImgDD)
     GenericFns gf;
     int grid_max = 1;
     unsigned char *d_images = nullptr;
@@ -200,7 +201,8 @@ struct perm_server_s {
         F.nmax = nmax;
         F.kind = kind;
         F.arith = ((kind >> 1) + 1) / 2;
-        F.words = F.arith == 0 ? 2 : F.arith;
+        F.words = result_words(F.arith);
+        F.img = kind == kKindDD ? kImgDD : (F.arith ? kImgInt : kImgF64);
         F.gf = generic_fns(nmax, kind);
         if (!F.gf.walk) return fail(PERM_ERR_INTERNAL, "no generic kernel for this family");
         F.K_target = tuned_chunk_log2(nmax, kind);
@@ -287,10 +289,12 @@ struct perm_server_s {
             r->out_offset = off;
             // the image goes up on stream 0 before any wave that reads it
             std::vector<unsigned char> img;
-            build_devmat(P.m, P.L, F.arith, F.nmax, img);
+            build_devmat(P.m, P.L, F.img, F.nmax, img);
             r->img_bytes = img.size();
-            cudaMemcpyAsync(F.d_images + (size_t)r->slot * F.gf.devmat_bytes, img.data(), img.size(),
-                            cudaMemcpyHostToDevice, streams[0]);
+            const cudaError_t e = debug_fail(kSiteUpload) ? cudaErrorInvalidValue
+                                  : cudaMemcpyAsync(F.d_images + (size_t)r->slot * F.gf.devmat_bytes, img.data(),
+                                                    img.size(), cudaMemcpyHostToDevice, streams[0]);
+            if (e != cudaSuccess) fail_request(r, cuda_fail(e, "serving: image upload"));
         }
         steps_active += steps;
         active.push_back(r);
@@ -322,11 +326,7 @@ struct perm_server_s {
         perm_result_t res;
         std::memset(&res, 0, sizeof(res));
         perm_status_t s = plan_device_setup(P);
-        if (s == PERM_OK) s = plan_launch(P, streams[0]);
-        if (s == PERM_OK) {
-            cudaError_t e = cudaStreamSynchronize(streams[0]);
-            s = e == cudaSuccess ? plan_finish(P, &res) : cuda_fail(e, "cudaStreamSynchronize");
-        }
+        if (s == PERM_OK) s = perm_compute(&P, streams[0], &res);   // applies precision AUTO too
         if (s != PERM_OK) res.status = s;
         lk.lock();
         steps_active -= (double)P.total;
@@ -383,15 +383,18 @@ struct perm_server_s {
             bm.out_offset = r->out_offset + first;
             bm.image = (int)((size_t)r->slot * F.gf.devmat_bytes / 16);
             bm.K = r->P->K;
+            bm.abs_shift = r->P->abs_shift;
             r->inflight_waves += 1;
             t += take;
         }
         w->parts = std::move(parts);
         w->stream = (int)(w - waves) % kStreams;
         cudaStream_t st = streams[w->stream];
-        cudaStreamWaitEvent(st, upload_done, 0);
-        cudaMemcpyAsync(w->d_table, w->h_table, sizeof(pk::BatchMat) * w->parts.size(), cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(w->d_counters, 0, 16, st);
+        cudaError_t e = cudaStreamWaitEvent(st, upload_done, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(w->d_table, w->h_table, sizeof(pk::BatchMat) * w->parts.size(), cudaMemcpyHostToDevice,
+                                st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w->d_counters, 0, 16, st);
         pk::BatchArgs ba;
         ba.mats = w->d_table;
         ba.devmats = F.d_images;
@@ -408,11 +411,22 @@ struct perm_server_s {
         ba.deadline_word = nullptr;
         ba.abort_flag = nullptr;
         int bps = 1;
-        F.gf.occ(256, slot_bytes, &bps);
+        if (e == cudaSuccess) e = F.gf.occ(256, slot_bytes, &bps);
         const uint64_t grid_occ = (uint64_t)kSMCount * std::max(bps, 1);
         const int grid = (int)std::min<uint64_t>(grid_occ, (t * 32 + 255) / 256);
-        F.gf.walk(ba, std::max(grid, 1), 256, st);
-        cudaEventRecord(w->done, st);
+        if (e == cudaSuccess) e = debug_fail(kSiteWaveLaunch) ? cudaErrorLaunchFailure : F.gf.walk(ba, std::max(grid, 1), 256, st);
+        if (e == cudaSuccess) e = cudaEventRecord(w->done, st);
+        if (e != cudaSuccess) {
+            // nothing of this wave counts: its requests fail instead of
+            // publishing whatever their result ranges hold
+            const perm_status_t fs = cuda_fail(e, "serving: wave launch");
+            for (Part &pt : w->parts) {
+                pt.req->inflight_waves -= 1;
+                fail_request(pt.req, fs);
+            }
+            w->parts.clear();
+            return true;
+        }
         w->busy = true;
         return true;
     }
@@ -436,10 +450,24 @@ struct perm_server_s {
             }
             f->family = fi;
             cudaStream_t st = streams[0];
-            cudaMemcpyAsync(f->d_seg, f->h_seg, 16 * cnt, cudaMemcpyHostToDevice, st);
-            segment_reduce_launch(F.arith, f->d_seg, (int)cnt, F.d_pool, f->d_res, st);
-            cudaMemcpyAsync(f->h_res, f->d_res, 32 * cnt, cudaMemcpyDeviceToHost, st);
-            cudaEventRecord(f->done, st);
+            cudaError_t e = cudaMemcpyAsync(f->d_seg, f->h_seg, 16 * cnt, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = debug_fail(kSiteFinish) ? cudaErrorLaunchFailure
+                                            : segment_reduce_launch(F.arith, f->d_seg, (int)cnt, F.d_pool, f->d_res, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(f->h_res, f->d_res, 32 * cnt, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(f->done, st);
+            if (e != cudaSuccess) {
+                const perm_status_t fs = cuda_fail(e, "serving: final reduction");
+                for (Request *r : f->reqs) {
+                    perm_result_t res;
+                    std::memset(&res, 0, sizeof(res));
+                    res.status = fs;
+                    retire(r);
+                    publish(r, res);
+                }
+                f->reqs.clear();
+                continue;
+            }
             f->busy = true;
         }
     }
@@ -448,6 +476,40 @@ struct perm_server_s {
         for (const Finish &f : finishes)
             if (f.busy && std::find(f.reqs.begin(), f.reqs.end(), r) != f.reqs.end()) return true;
         return false;
+    }
+
+    // Marks a request failed: nothing more of it is scheduled, and it is
+    // published with `st` once none of its waves or reductions is in flight.
+    void fail_request(Request *r, perm_status_t st) {
+        if (!r->failed) r->fail_status = st;
+        r->failed = true;
+        r->next_task = r->ntasks;
+    }
+
+    // Precision AUTO: an FP64 request whose result proved too ill-conditioned
+    // gives back its slot and result range and goes to the front of the queue
+    // as a double-double request.  False if that family cannot be set up.
+    bool requeue_dd(Request *r) {
+        perm_plan_s &P = *r->P;
+        if (P.m.is_int || P.dd || opts.precision != PERM_PREC_AUTO || P.m.n > kAutoDDMaxN || r->family < 0) return false;
+        Family &F = fam[r->family];
+        F.free_slots.push_back(r->slot);
+        F.ranges.release(r->out_offset, r->ntasks);
+        steps_active -= (double)P.total;
+        auto it = std::find(active.begin(), active.end(), r);
+        if (it != active.end()) active.erase(it);
+        const int nmax = nmax_bucket(P.m.n);
+        P.dd = true;
+        r->family = family_index(nmax, P.kind());
+        r->slot = -1;
+        r->ntasks = r->next_task = r->done_tasks = 0;
+        r->inflight_waves = 0;
+        if (ensure_family(r->family, nmax, P.kind()) != PERM_OK) {
+            r->retired = true;   // holds nothing any more
+            return false;
+        }
+        queue.push_front(r);
+        return true;
     }
 
     void retire(Request *r) {
@@ -481,24 +543,7 @@ struct perm_server_s {
             if (opts.timeout_ms > 0) {
                 const double t = now_ms();
                 for (Request *r : active)
-                    if (!r->failed && t - r->t_submit > opts.timeout_ms) {
-                        r->failed = true;
-                        r->fail_status = PERM_ERR_TIMEOUT;
-                        r->next_task = r->ntasks;   // schedule nothing more
-                    }
-                for (size_t i = 0; i < active.size(); ++i) {
-                    Request *r = active[i];
-                    if (r->failed && r->inflight_waves == 0 && r->family >= 0 &&
-                        std::find(ready[r->family].begin(), ready[r->family].end(), r) == ready[r->family].end() &&
-                        !in_finish(r)) {
-                        perm_result_t res;
-                        std::memset(&res, 0, sizeof(res));
-                        res.status = r->fail_status;
-                        retire(r);
-                        publish(r, res);
-                        --i;
-                    }
-                }
+                    if (!r->failed && t - r->t_submit > opts.timeout_ms) fail_request(r, PERM_ERR_TIMEOUT);
                 // a timed-out request waiting in the queue fails there
                 for (auto it = queue.begin(); it != queue.end();) {
                     if (t - (*it)->t_submit > opts.timeout_ms) {
@@ -512,16 +557,36 @@ struct perm_server_s {
                     }
                 }
             }
+            // failed requests (timeout, a failed upload or launch) are published
+            // once none of their waves or reductions is in flight
+            for (size_t i = 0; i < active.size(); ++i) {
+                Request *r = active[i];
+                if (r->failed && r->inflight_waves == 0 && r->family >= 0 &&
+                    std::find(ready[r->family].begin(), ready[r->family].end(), r) == ready[r->family].end() &&
+                    !in_finish(r)) {
+                    perm_result_t res;
+                    std::memset(&res, 0, sizeof(res));
+                    res.status = r->fail_status;
+                    retire(r);
+                    publish(r, res);
+                    --i;
+                }
+            }
             bool launched = false;
             for (size_t fi = 0; fi < fam.size(); ++fi)
                 if (fam[fi].ready) while (launch_wave((int)fi)) launched = true;
-            // harvest finished waves
+            // harvest finished waves (a wave whose event reports an error fails
+            // its requests)
             bool progressed = false;
             for (Wave &w : waves) {
-                if (!w.busy || cudaEventQuery(w.done) != cudaSuccess) continue;
+                if (!w.busy) continue;
+                const cudaError_t q = cudaEventQuery(w.done);
+                if (q == cudaErrorNotReady) continue;
+                const perm_status_t fs = q == cudaSuccess ? PERM_OK : cuda_fail(q, "serving: wave");
                 for (Part &pr : w.parts) {
                     pr.req->done_tasks += pr.count;
                     pr.req->inflight_waves -= 1;
+                    if (fs != PERM_OK) fail_request(pr.req, fs);
                 }
                 for (Part &pr : w.parts) {
                     Request *r = pr.req;
@@ -547,14 +612,21 @@ struct perm_server_s {
                 if (!ready[fi].empty()) launch_finish((int)fi, ready[fi]);
             // harvest finished reductions
             for (Finish &f : finishes) {
-                if (!f.busy || cudaEventQuery(f.done) != cudaSuccess) continue;
+                if (!f.busy) continue;
+                const cudaError_t q = cudaEventQuery(f.done);
+                if (q == cudaErrorNotReady) continue;
+                const perm_status_t fs = q == cudaSuccess ? PERM_OK : cuda_fail(q, "serving: final reduction");
                 for (size_t i = 0; i < f.reqs.size(); ++i) {
                     Request *r = f.reqs[i];
                     perm_result_t res;
                     r->P->grid = fam[f.family].grid_max;
                     r->P->block = 256;
                     describe(*r->P, &res);
-                    finish_raw(*r->P, f.h_res + 4 * i, &res);
+                    if (fs != PERM_OK) res.status = fs;
+                    else finish_raw(*r->P, f.h_res + 4 * i, &res);
+                    if (fs == PERM_OK && res.status == PERM_OK && !r->P->m.is_int && !r->P->dd &&
+                        needs_dd(r->P->m.n, res.f64 + res.f64_lo, res.abs_term_sum) && requeue_dd(r))
+                        continue;
                     retire(r);
                     publish(r, res);
                 }
@@ -600,6 +672,7 @@ perm_status_t perm_server_create(const perm_server_opts_t *opts, perm_server_t *
     if (s->opts.max_n <= 0) s->opts.max_n = 40;
     if (s->opts.max_n > 64) return fail(PERM_ERR_ARG, "max_n must be <= 64");
     if (s->opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
+    if (s->opts.precision < PERM_PREC_AUTO || s->opts.precision > PERM_PREC_DD) return fail(PERM_ERR_ARG, "bad precision");
     s->device = s->opts.device;
     s->step_budget = s->opts.step_budget > 0 ? s->opts.step_budget : 1.5e11;
     perm_status_t st = s->init_device();
@@ -616,7 +689,10 @@ perm_status_t perm_submit(perm_server_t s, const perm_matrix_t *A, uint64_t *tic
     if (!r) return fail(PERM_ERR_NOMEM, "out of host memory");
     r->P.reset(new (std::nothrow) perm_plan_s());
     if (!r->P) return fail(PERM_ERR_NOMEM, "out of host memory");
-    perm_status_t st = plan_prepare(A, nullptr, *r->P);
+    perm_opts_t po;
+    std::memset(&po, 0, sizeof(po));
+    po.precision = s->opts.precision;
+    perm_status_t st = plan_prepare(A, &po, *r->P);
     if (st != PERM_OK) return st;
     perm_plan_s &P = *r->P;
     r->t_submit = now_ms();

@@ -1,0 +1,150 @@
+"""Host emulation of generated kernels: the CUDA C++ that the code generator
+emits for a matrix (with core.cuh) is compiled as plain host C++ under
+AddressSanitizer and UndefinedBehaviorSanitizer, and each 2^K-step chunk of the
+Gray walk is run as one lane (warp votes and shuffles reduce to the lane's own
+value).  Every chunk's partial sum is compared with the oracle's sum over the
+same Gray range (Algorithm 1 with doubled x, modulo the kernel's ring; or in
+long double for FP64).  It is built twice, with automatic variables
+initialised to zero and to a byte pattern: a read of an uninitialised value
+that mattered would make the two disagree.  This pins the generated code's
+logic and its freedom from undefined behaviour independently of any GPU
+compiler (test infrastructure; no GPU needed)."""
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_15126_gb300 import _abi as A
+from paper_2501_15126_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2501_15126_gb300", "csrc")
+U = 2.0 ** -53
+
+HARNESS = r'''
+#include "shim.h"
+#include "walk.cu"
+#include <cstdio>
+#include <cstdlib>
+int main(int argc, char **argv) {
+    const int K = std::atoi(argv[1]);
+    static pk::GenPol::X xg[64];
+    pk::GenPol pol;
+    pol.xg = xg;
+    pol.stride = 1;
+    unsigned long long q;
+    while (std::scanf("%llu", &q) == 1) {
+        unsigned long long skipped = 0, w[6] = {0, 0, 0, 0, 0, 0};
+        const auto acc = pk::walk_chunk<pk::GenPol, pk::A, 5>(pol, q, K, 1, skipped);
+        pk::A::acc_store(w, acc);
+        std::printf("%llu", q);
+        for (int i = 0; i < pk::A::ACC_WORDS; ++i) std::printf(" %016llx", w[i]);
+        std::printf("\n");
+    }
+    return 0;
+}
+'''
+
+
+def emulate(source, K, chunks, init):
+    """Compiles the generated source with the harness (sanitizers on) and runs
+    the given chunks; returns {q: [words]}."""
+    with tempfile.TemporaryDirectory() as d:
+        open(os.path.join(d, "walk.cu"), "w").write(source)
+        open(os.path.join(d, "main.cpp"), "w").write(HARNESS)
+        exe = os.path.join(d, "walk")
+        subprocess.check_call(["g++", "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined",
+                               "-fno-sanitize-recover=all", "-ftrivial-auto-var-init=" + init,
+                               "-I", os.path.join(HERE, "host_emulation"), "-I", CSRC, "-I", d,
+                               os.path.join(d, "main.cpp"), "-o", exe])
+        out = subprocess.run([exe, str(K)], input=" ".join(map(str, chunks)), capture_output=True, text=True,
+                             check=True).stdout
+    res = {}
+    for line in out.splitlines():
+        f = line.split()
+        res[int(f[0])] = [int(x, 16) for x in f[1:]]
+    return res
+
+
+def plan_order(a, **kw):
+    ins = A.inspect(a, **{k: v for k, v in kw.items() if k == "ordering"})
+    return np.ascontiguousarray(a[:, list(ins.col_order)[: a.shape[0]]])
+
+
+def ring_limbs(source):
+    m = re.search(r"typedef ArithExact<(\d+)> A;", source)
+    return int(m.group(1)) if m else 0
+
+
+def check_exact(a, K, chunks, **kw):
+    src = A.codegen_source(a, engine=A.PERM_ENGINE_CODEGEN, **kw)
+    limbs = ring_limbs(src)
+    mask = (1 << min(128, 32 * limbs)) - 1   # the oracle is exact modulo 2^128
+    ao = plan_order(a, **kw)
+    got = {init: emulate(src, K, chunks, init) for init in ("zero", "pattern")}
+    for q in chunks:
+        want = oracle.nw2_range(ao, q << K, (q + 1) << K) & mask
+        for init in got:
+            v = sum(w << (64 * i) for i, w in enumerate(got[init][q])) & mask
+            assert v == want, (init, q)
+
+
+def check_f64(a, K, chunks, **kw):
+    src = A.codegen_source(a, engine=A.PERM_ENGINE_CODEGEN, **kw)
+    assert "typedef ArithF64 A;" in src
+    ao = plan_order(a, **kw)
+    n = a.shape[0]
+    sh = int(re.search(r"static constexpr int abs_shift = (-?\d+);", src).group(1))
+    got = {init: emulate(src, K, chunks, init) for init in ("zero", "pattern")}
+    for q in chunks:
+        s, sa = oracle.nw_range(ao, q << K, (q + 1) << K)
+        for init in got:
+            hi, lo, ab = (np.array(got[init][q], dtype=np.uint64).view(np.float64))
+            assert abs(hi + lo - float(s)) <= 64 * n * U * float(sa), (init, q)
+            assert abs(np.ldexp(ab, sh) - float(sa)) <= 1e-4 * float(sa), (init, q)
+
+
+def test_negated_ones_in_a_128_bit_ring_with_and_without_folding(monkeypatch):
+    """-J_15 with exact_words = 2 (a 128-bit ring): every chunk of the whole
+    walk, with rows folded in 32 bits and with one ring product per row (the
+    form that once returned a wrong top limb on the GPU when built for 128
+    registers)."""
+    a = -synth.ones(15)
+    chunks = list(range(0, 1 << 14 >> 8))
+    check_exact(a, 8, chunks, exact_words=2)
+    monkeypatch.setenv("PERM_CODEGEN_NO_FOLD", "1")
+    src = A.codegen_source(a, engine=A.PERM_ENGINE_CODEGEN, exact_words=2)
+    assert "x[0] * x[1]" not in src
+    check_exact(a, 8, chunks, exact_words=2)
+
+
+def test_ones_in_a_192_bit_ring():
+    """J_30 in a 192-bit ring (the kernel that spills most at 128 registers):
+    chunks spread over the walk, including the last one."""
+    a = synth.ones(30)
+    K = 10
+    last = (1 << 29 >> K) - 1
+    check_exact(a, K, [0, 1, 7, 1000, 123457 % last, last // 2, last], exact_words=3)
+
+
+def test_band_plus_off_band_exact_with_global_rows():
+    """The n=48 band |i-j| <= 3 plus 2 off-band nonzeros per row, 0/1, with 20
+    rows of x in registers and the rest in global memory (Algorithm 4's split):
+    chunks with high Gray bits set."""
+    a = synth.band_plus(48, 3, 2, seed=3, values="01")
+    K = 9
+    top = (1 << 47) >> K
+    check_exact(a, K, [0, 5, top // 3, top - 1], reg_rows=20)
+
+
+@pytest.mark.parametrize("flags", [0, 4])
+def test_generated_f64_walks(flags):
+    """FP64 generated kernels (two-state chains, and the paired chain with
+    flags = PERM_FLAG_PAIRED_CHAIN): chunk sums within the FP64 rounding bound
+    of the oracle's, and their sums of |terms| within 1e-4."""
+    a = synth.single_er(24, 0.2, 1, values="f64")
+    check_f64(a, 9, [0, 3, 1000, (1 << 23 >> 9) - 1], flags=flags)
