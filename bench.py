@@ -256,14 +256,41 @@ def extras(A, sh, a, first):
         "cfg4_batch_sampled": out["batch"].get("accuracy_vs_oracle"),
         "cfg5_serving_sampled": out["serving"].get("accuracy_vs_oracle"),
         "cfg3_n48": "whole 2^47-step exact walks: bench.py --workload cfg3 (profiles/cfg3_n48_full_permanent.md)"}
+    out["exact_roofline"] = exact_roofline(A, sh)
     out["cpu_fp64_baseline"] = cpu_fp64_baseline(a)
     return out
 
 
-def config_block(engine, steps_per_step):
+def exact_roofline(A, sh):
+    """The exact path against the integer issue roofline: counted integer
+    multiply operations per Gray step (the ring-op cost model,
+    perm_inspect_t.ring_ops_per_step) x steps / kernel time, over the IMAD
+    rate measured on this GPU: cfg1 (n=24 0/1, the plan the library picks) and
+    the n=48 band's generated exact kernel on a 2^30-step prefix."""
+    from paper_2501_15126_gb300 import synth
+    _, imad = A.issue_rates(sh)
+    out = {"bound": "alu (IMAD)", "peak_imad_ops_per_s": imad}
+    for name, a, kw in (("cfg1_n24_01", synth.single_er(24, 0.2, 1, values="01"), {}),
+                        ("n48_band_01_prefix_2^30", synth.band_plus(48, 3, 2, seed=3, values="01"),
+                         dict(g_lo=0, g_hi=1 << 30, engine=A.PERM_ENGINE_CODEGEN))):
+        p = A.Plan(a, **kw)
+        r = p.compute(sh)
+        ms = min(p.compute(sh).ms_kernel for _ in range(5))
+        p.close()
+        ach = r.fp_ops_per_step * r.steps / (ms / 1e3)
+        out[name] = {"engine": "codegen" if r.engine == A.PERM_ENGINE_CODEGEN else "generic", "ms": ms,
+                     "gray_steps_per_s": r.steps / (ms / 1e3), "ring_ops_per_step": r.fp_ops_per_step,
+                     "achieved_imad_ops_per_s": ach, "frac": ach / imad, "zero_skip_frac": r.zero_skip_frac,
+                     "exact_words": r.exact_words, "regs": r.regs_per_thread}
+    return out
+
+
+def config_block(engine, steps_per_step, shard=False):
     return {"workload": "single real sparse matrix n=36: ER p=0.15 + forced diagonal, (0,1] values, shuffled "
                         "columns, seed 2", "n": 36, "gray_steps_per_step": steps_per_step, "engine": engine,
-            "l2": "flushed between steps (256 MiB device write)", "parallelism": "replicas (one matrix per GPU)"}
+            "l2": "flushed between steps (256 MiB device write)",
+            "parallelism": ("Gray-range shards: one permanent split across the GPUs, partial sums combined once"
+                            if shard else "replicas (one matrix per GPU)")}
 
 
 def run_ours(args):
@@ -282,7 +309,14 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     fp64_rate, imad_rate = A.issue_rates(sh)
-    plan = A.Plan(a)                       # ordering, partitioning, NVRTC (warm-up region)
+    shard = args.shard and world > 1
+    if shard:
+        # one permanent split across the ranks: each walks its Gray shard (Sec. II-A)
+        from paper_2501_15126_gb300 import dist as pd
+        lo, hi = pd.shard_range(GRAY_STEPS, world, rank)
+        plan = A.Plan(a, g_lo=lo, g_hi=hi)
+    else:
+        plan = A.Plan(a)                   # ordering, partitioning, NVRTC (warm-up region)
     first = plan.compute(sh)
     for _ in range(max(args.warmup - 1, 0)):
         plan.compute(sh)
@@ -309,9 +343,13 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     total_ms = sum(step_ms)
+    combined = None
     if world > 1:
         from paper_2501_15126_gb300 import dist as pd
         total_ms = pd.max_over_ranks(total_ms, device=dev)
+        if shard:   # the shards' partial sums, combined on every rank
+            s_hi, s_lo = pd.combine_f64(first.f64, first.f64_lo, device=dev)
+            combined = (s_hi + s_lo) * (2.0 if N36["n"] % 2 else -2.0)
         torch.distributed.barrier()
 
     # end to end through the public API from host memory, every step
@@ -320,25 +358,27 @@ def run_ours(args):
         t0 = time.perf_counter()
         rr = A.permanent(a, stream=sh)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        assert rr.value == first.value
+        assert shard or rr.value == first.value
     plan_engine = "codegen" if first.engine == A.PERM_ENGINE_CODEGEN else "generic"
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
-    value = world * args.steps * GRAY_STEPS / (total_ms / 1e3)
+    # replicas: every rank walks a whole permanent; shards: the ranks walk one together
+    value = (1 if shard else world) * args.steps * GRAY_STEPS / (total_ms / 1e3)
     mean_kernel_ms = statistics.mean(kern_ms)
     ops = first.fp_ops_per_step * GRAY_STEPS
     achieved = ops / (mean_kernel_ms / 1e3)
     kh = kernel_hash()
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_block(plan_engine, GRAY_STEPS),
+        "config": config_block(plan_engine, GRAY_STEPS, shard),
         "ms_per_permanent": total_ms / args.steps,
-        "permanent": first.value,
+        "permanent": combined if shard else first.value,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": NOMINAL_FP64_ISSUE / 1e9,
                      "unit": "G FP64 op/s", "frac": achieved / NOMINAL_FP64_ISSUE,
                      "peak_measured": fp64_rate / 1e9, "frac_of_measured": achieved / fp64_rate,
@@ -604,8 +644,9 @@ def run_ablation(args):
         base = rec["codegen_chain"]["ms"]
         for ename in rec:
             rec[ename]["chain_speedup_over_this"] = rec[ename]["ms"] / base
-        vals = [rec[e]["value"] for e in rec]
-        rec["max_rel_spread_of_values"] = (max(vals) - min(vals)) / abs(vals[0])
+        if not hi:   # whole walks agree up to rounding (a prefix's partial sum depends on the column order)
+            vals = [rec[e]["value"] for e in rec]
+            rec["max_rel_spread_of_values"] = (max(vals) - min(vals)) / abs(vals[0])
         rec["gray_steps"] = (hi - lo) if hi else 1 << (a.shape[0] - 1)
         out["cases"][name] = rec
         print(json.dumps({name: rec}), flush=True)
@@ -660,6 +701,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split each permanent's Gray range across the ranks (strong scaling) "
+                         "instead of one permanent per rank")
     ap.add_argument("--no-extras", action="store_true",
                     help="single workload: only the headline (no batch, serving, accuracy, cold e2e, FP64 CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

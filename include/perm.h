@@ -160,6 +160,11 @@ typedef struct {
                            /*   PERM_ERR_TIMEOUT (the context stays usable); 0 = none      */
     int32_t precision;     /* PERM_PREC_*: arithmetic of FP64 inputs (sub-ranges and       */
                            /*   checkpointed runs: AUTO means FP64)                         */
+    int32_t shared_rows;   /* codegen: of the rows beyond reg_rows, this many live in      */
+                           /*   shared memory (x[(slot - k) * 256 + thread] per block), the */
+                           /*   rest in global memory -- the three-level placement of the  */
+                           /*   Gray-frequency order (Sec. V, Sec. VIII); 0 = none         */
+    int32_t reserved2;
 } perm_opts_t;
 
 /* Result of one permanent (or one Gray sub-range). */
@@ -187,7 +192,9 @@ typedef struct {
     double ms_plan;        /* host preprocessing                                      */
     double ms_compile;     /* NVRTC + module load (0 when cached or generic)          */
     double ms_kernel;      /* device time of the walk + reduction (CUDA events)       */
-    double fp_ops_per_step;/* counted arithmetic ops per Gray step (cost model)       */
+    double fp_ops_per_step;/* counted arithmetic ops per Gray step (cost model): FP64 */
+                           /*   operations, or on the exact path integer multiply     */
+                           /*   operations (perm_inspect_t.ring_ops_per_step)         */
     double zero_skip_frac; /* fraction of 2^B-step blocks skipped as all-zero         */
     /* FP64 inputs: sum over the walk's Gray indices of |prod_i x_i(g)|, times 2 for
        a whole walk (the scale of the permanent), raw for a sub-range.  It is
@@ -200,7 +207,7 @@ typedef struct {
     double abs_term_sum;
     int32_t precision;     /* FP64 inputs: PERM_PREC_F64 or PERM_PREC_DD that produced */
                            /*   the value; 0 for integer inputs                         */
-    int32_t reserved2;
+    int32_t shared_rows;   /* codegen: rows of x in shared memory                      */
 } perm_result_t;
 
 typedef struct perm_plan_s *perm_plan_t;
@@ -224,10 +231,13 @@ perm_status_t perm_compute(perm_plan_t plan, void *stream, perm_result_t *out);
 /* Frees a plan (NULL is allowed). */
 void perm_plan_destroy(perm_plan_t plan);
 
-/* Computes `count` permanents in one persistent launch fed by a device work
-   queue (the matrices may differ in n and value type).  out has `count`
-   entries; out[i].status reports each matrix on its own.  opts applies to
-   every matrix (sub-ranges are not allowed here).
+/* Computes `count` permanents in one persistent launch per kernel family
+   (NMAX bucket x arithmetic) fed by a device work queue (the matrices may
+   differ in n and value type); the families' launches are captured as one
+   CUDA graph (PERM_FLAG_NO_GRAPH launches them directly).  Precision AUTO
+   reruns the ill-conditioned FP64 matrices in double-double as one more
+   launch.  out has `count` entries; out[i].status reports each matrix on its
+   own.  opts applies to every matrix (sub-ranges are not allowed here).
    Errors: ARG, SIZE, CUDA, NOMEM (per-matrix PATTERN/OVERFLOW go to out[i]). */
 perm_status_t perm_batch(const perm_matrix_t *mats, int32_t count, const perm_opts_t *opts,
                          void *stream, perm_result_t *out);
@@ -329,6 +339,10 @@ typedef struct {
     int32_t reserved0;
     double ops_per_step_walk;    /* cost model of the scheme the walk runs (FP64:     */
                                  /*   two-state or paired chain; exact: one chain)    */
+    double ring_ops_per_step;    /* exact inputs: integer multiply operations per step */
+                                 /*   of the generated walk (its rows folded in 32 bits */
+                                 /*   as the generator folds them), in the ring of     */
+                                 /*   exact_limbs limbs; 0 for FP64 inputs             */
 } perm_inspect_t;
 
 perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts, perm_inspect_t *out);

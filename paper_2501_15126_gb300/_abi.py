@@ -40,7 +40,8 @@ class Matrix(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("ordering", c_i32), ("engine", c_i32), ("reg_rows", c_i32), ("chunk_log2", c_i32),
                 ("threads", c_i32), ("exact_words", c_i32), ("zero_skip", c_i32), ("flags", c_i32),
-                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64), ("timeout_ms", c_i32), ("precision", c_i32)]
+                ("gr_ratio", c_dbl), ("g_lo", c_u64), ("g_hi", c_u64), ("timeout_ms", c_i32), ("precision", c_i32),
+                ("shared_rows", c_i32), ("reserved2", c_i32)]
 
 
 class Result(ctypes.Structure):
@@ -50,7 +51,7 @@ class Result(ctypes.Structure):
                 ("reg_cols", c_i32), ("chunk_log2", c_i32), ("threads", c_i32), ("regs_per_thread", c_i32),
                 ("steps", c_u64), ("ms_plan", c_dbl), ("ms_compile", c_dbl), ("ms_kernel", c_dbl),
                 ("fp_ops_per_step", c_dbl), ("zero_skip_frac", c_dbl), ("abs_term_sum", c_dbl),
-                ("precision", c_i32), ("reserved2", c_i32)]
+                ("precision", c_i32), ("shared_rows", c_i32)]
 
     @property
     def exact(self) -> int:
@@ -73,7 +74,7 @@ class Inspect(ctypes.Structure):
                 ("group_size", c_i32 * 64), ("col_nnz", c_i32 * 64), ("reg_rows", c_i32), ("reg_cols", c_i32),
                 ("exact_words", c_i32), ("bound_log2", c_dbl), ("ops_per_step", c_dbl),
                 ("ops_per_step_paper", c_dbl), ("exact_limbs", c_i32), ("reserved0", c_i32),
-                ("ops_per_step_walk", c_dbl)]
+                ("ops_per_step_walk", c_dbl), ("ring_ops_per_step", c_dbl)]
 
 
 class ServerOpts(ctypes.Structure):

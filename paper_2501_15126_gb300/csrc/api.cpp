@@ -244,6 +244,7 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     if (opts.threads < 0) return fail(PERM_ERR_ARG, "threads < 0");
     if (opts.timeout_ms < 0) return fail(PERM_ERR_ARG, "timeout_ms < 0");
     if (opts.precision < PERM_PREC_AUTO || opts.precision > PERM_PREC_DD) return fail(PERM_ERR_ARG, "bad precision");
+    if (opts.shared_rows < 0) return fail(PERM_ERR_ARG, "shared_rows < 0");
     P.zero = !has_perfect_matching(P.m);
     if (!P.m.is_int) {
         P.abs_shift = abs_shift_for(P.m);
@@ -351,6 +352,10 @@ static void codegen_layout(perm_plan_s &P) {
     if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
     normalise_split(P.L, &k, &c);
     P.pure_reg = (P.opts.flags & PERM_FLAG_PURE_REG) != 0;
+    // the middle tier: shared memory holds up to 96 KB of x per 256-thread block
+    // (two blocks per SM), i.e. 48 FP64 or 96 int32 rows
+    const int cap = (int)(96 * 1024 / (256 * (P.arith == 0 ? 8 : 4)));
+    P.k2 = P.pure_reg ? 0 : std::max(0, std::min({P.opts.shared_rows, n - k, cap}));
     // sum|terms| costs the generated FP64 kernels about a tenth of their speed:
     // they keep it where precision AUTO may need it (whole walks of n <= 32),
     // or when asked (PERM_FLAG_ABS_SUM)
@@ -438,8 +443,8 @@ perm_status_t plan_device_setup(perm_plan_s &P) {
         if (st != PERM_OK) return fail(st, err);
         st = choose_launch(P, P.cg.block_log2, std::max(P.cg.blocks_per_sm, 1), P.cg.block);
         if (st != PERM_OK) return st;
-        if (P.k < n) {
-            const size_t bytes = (size_t)(n - P.k) * (size_t)P.grid * P.block * (P.arith == 0 ? 8 : 4);
+        if (P.k + P.k2 < n) {
+            const size_t bytes = (size_t)(n - P.k - P.k2) * (size_t)P.grid * P.block * (P.arith == 0 ? 8 : 4);
             if ((e = cudaMalloc(&P.d_xglob, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(x global rows)");
         }
     }
@@ -542,6 +547,7 @@ void describe(const perm_plan_s &P, perm_result_t *out) {
     out->ordering = P.L.ordering;
     out->reg_rows = P.engine == PERM_ENGINE_CODEGEN ? P.k : n;
     out->reg_cols = P.engine == PERM_ENGINE_CODEGEN ? P.c : n - 1;
+    out->shared_rows = P.engine == PERM_ENGINE_CODEGEN ? P.k2 : 0;
     out->chunk_log2 = P.K;
     out->threads = P.grid * P.block;
     out->regs_per_thread = P.regs;
@@ -550,7 +556,12 @@ void describe(const perm_plan_s &P, perm_result_t *out) {
     out->ms_compile = P.ms_compile;
     out->fp_ops_per_step = (P.engine == PERM_ENGINE_GENERIC && !P.direct && P.arith == 0 && P.m.n <= 32)
                                ? cost_per_step_dual(P.L, true)
-                               : P.ops_per_step;
+                           : P.engine == PERM_ENGINE_XSHARED ? P.ops_per_step_paper   // a full product every step
+                                                             : P.ops_per_step;
+    if (P.m.is_int && !P.zero) {   // integer multiply operations of the kernel that runs
+        const int fold = P.engine == PERM_ENGINE_CODEGEN ? (codegen_no_fold() ? 0 : 1) : (P.fold ? 2 : 0);
+        out->fp_ops_per_step = ring_ops_per_step(P.m, P.L, P.limbs, fold);
+    }
     out->exact_words = P.m.is_int ? P.arith : 0;
     out->precision = P.m.is_int ? 0 : (P.dd ? PERM_PREC_DD : PERM_PREC_F64);
 }
@@ -826,6 +837,7 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     out->exact_words = m.is_int ? exact_words_for(out->bound_log2, m.n) : 0;
     out->exact_limbs = out->exact_words ? exact_limbs_for(out->bound_log2, m.n) : 0;
     out->ops_per_step_walk = walk_cost_per_step(L, !m.is_int);
+    out->ring_ops_per_step = m.is_int && out->exact_limbs ? ring_ops_per_step(m, L, out->exact_limbs, 1) : 0.0;
     out->ops_per_step = cost_per_step(L, false);
     out->ops_per_step_paper = cost_per_step(L, true);
     return PERM_OK;

@@ -144,6 +144,55 @@ using namespace perm;
 
 namespace perm {
 
+// The batch's device work captured as one CUDA graph on a library stream:
+// `st` is joined to it with events before and after, so the caller's stream
+// (the legacy default stream included, which cannot be captured) sees the
+// usual ordering.
+struct GraphLaunch {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t before = nullptr, after = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool capture(std::map<std::pair<int, int>, BatchGroup> &groups, int zero_skip, cudaStream_t) {
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail_clean();
+        if (cudaEventCreateWithFlags(&before, cudaEventDisableTiming) != cudaSuccess) return fail_clean();
+        if (cudaEventCreateWithFlags(&after, cudaEventDisableTiming) != cudaSuccess) return fail_clean();
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail_clean();
+        bool ok = true;
+        for (auto &kv : groups) ok = ok && kv.second.launch(cs, zero_skip) == PERM_OK;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (!ok || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return fail_clean();
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { exec = nullptr; return fail_clean(); }
+        return true;
+    }
+    cudaError_t launch(cudaStream_t st) {
+        cudaError_t e = cudaEventRecord(before, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, before, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(after, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, after, 0);
+        return e;
+    }
+    bool fail_clean() {
+        cudaGetLastError();   // a failed capture leaves no sticky error behind
+        return false;
+    }
+    ~GraphLaunch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        if (before) cudaEventDestroy(before);
+        if (after) cudaEventDestroy(after);
+    }
+};
+
 // Launches every group (one persistent walk and one segmented reduction
 // each, all in one device arena), reads the results back and finishes
 // out[i] for every matrix of the groups.
@@ -183,8 +232,19 @@ static perm_status_t run_groups(std::map<std::pair<int, int>, BatchGroup> &group
     if ((e = cudaEventRecord(ev.e0, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (auto &kv : groups) {
         perm_status_t s = (perm_status_t)kv.second.upload(st);
-        if (s == PERM_OK) s = (perm_status_t)kv.second.launch(st, opts.zero_skip ? 0 : 1);
         if (s != PERM_OK) return s;
+    }
+    // every family's launches (counter reset, walk, reduction) as one CUDA
+    // graph; launched directly if the capture is not possible
+    GraphLaunch gl;
+    const bool graphed = !(opts.flags & PERM_FLAG_NO_GRAPH) && gl.capture(groups, opts.zero_skip ? 0 : 1, st);
+    if (!graphed) {
+        for (auto &kv : groups) {
+            const perm_status_t s = (perm_status_t)kv.second.launch(st, opts.zero_skip ? 0 : 1);
+            if (s != PERM_OK) return s;
+        }
+    } else if ((e = gl.launch(st)) != cudaSuccess) {
+        return cuda_fail(e, "batch graph launch");
     }
     if ((e = cudaEventRecord(ev.e1, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     // results back in one copy per group, then the group's counters

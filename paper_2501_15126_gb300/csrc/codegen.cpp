@@ -54,6 +54,7 @@ struct Driver {
     CUresult (*occupancy)(int *, CUfunction, int, size_t) = nullptr;
     CUresult (*getErrorString)(CUresult, const char **) = nullptr;
     CUresult (*moduleUnload)(CUmodule) = nullptr;
+    CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
     bool ok = false;
 };
 
@@ -75,7 +76,8 @@ Driver &driver() {
         d.ok = entry("cuModuleLoadData", d.moduleLoadData) && entry("cuModuleGetFunction", d.moduleGetFunction) &&
                entry("cuLaunchKernel", d.launchKernel) && entry("cuFuncGetAttribute", d.funcGetAttribute) &&
                entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", d.occupancy) &&
-               entry("cuGetErrorString", d.getErrorString) && entry("cuModuleUnload", d.moduleUnload);
+               entry("cuGetErrorString", d.getErrorString) && entry("cuModuleUnload", d.moduleUnload) &&
+               entry("cuFuncSetAttribute", d.funcSetAttribute);
     });
     return d;
 }
@@ -100,7 +102,7 @@ int codegen_min_blocks(const perm_plan_s &) {
 }
 // PERM_CODEGEN_NO_FOLD=1: exact kernels multiply every row into the ring on
 // its own (no 32-bit folding), as they did before folding was introduced.
-bool codegen_no_fold() {
+bool no_fold_env() {
     const char *e = std::getenv("PERM_CODEGEN_NO_FOLD");
     return e && std::atoi(e) == 1;
 }
@@ -118,10 +120,10 @@ std::string lit(const perm_plan_s &P, double v) {
 
 struct Emitter {
     const perm_plan_s &P;
-    int n, k, c;
+    int n, k, c, k2;
     int min_blocks;   // __launch_bounds__ minimum resident blocks per SM (register budget)
     std::ostringstream o;
-    Emitter(const perm_plan_s &p, int mb) : P(p), n(p.m.n), k(p.k), c(p.c), min_blocks(mb) {}
+    Emitter(const perm_plan_s &p, int mb) : P(p), n(p.m.n), k(p.k), c(p.c), k2(p.k2), min_blocks(mb) {}
 
     // value of ordered column p at slot s (doubled on the exact path)
     bool has(int p, int s) const { return (P.L.colmask[p] >> s) & 1ull; }
@@ -131,7 +133,8 @@ struct Emitter {
     }
     std::string slot(int s) const {
         if (s < k) return "x[" + std::to_string(s) + "]";
-        return "xg[" + std::to_string(s - k) + "ull * stride]";
+        if (s < k + k2) return "xs[" + std::to_string(s - k) + "u * 256u]";   // the block's shared tier
+        return "xg[" + std::to_string(s - k - k2) + "ull * stride]";
     }
     // one update of slot s by column p; mode 1/-1 = static sign, 0 = runtime s
     void update(int p, int s, int mode, const char *ind) {
@@ -160,7 +163,7 @@ struct Emitter {
     void group_product(int g, const char *ind) { product_range(P.L.group_begin[g], P.L.group_begin[g + 1], ind); }
     // q *= the slots [b, e), folded in 32 bits on the exact path
     void product_range(int b, int e, const char *ind) {
-        if (P.arith == 0 || codegen_no_fold()) {
+        if (P.arith == 0 || no_fold_env()) {
             for (int s = b; s < e; ++s) o << ind << "q = A::mul(q, " << slot(s) << ");\n";
             return;
         }
@@ -281,7 +284,7 @@ struct Emitter {
         o << "    static constexpr bool kDual = " << (P.dual ? "true" : "false") << ";\n";
         o << "    static constexpr bool kUnrolledDual = true;\n";
         o << "    typedef A::X X;\n    typedef A::P P;\n";
-        o << "    X *xg;\n    unsigned long long stride;\n";
+        o << "    X *xg;\n    unsigned long long stride;\n    X *xs;\n";
         // sum|terms| is accumulated as sum|terms| 2^-abs_shift (core.cuh); the
         // paired step scales its column-0 products by 2^-SH0 and Q_1 by the rest
         o << "    static constexpr int abs_shift = " << (P.arith == 0 ? P.abs_shift : 0) << ";\n";
@@ -467,7 +470,9 @@ struct Emitter {
     void emit_kernel(int B) {
         o << "extern \"C\" __global__ void __launch_bounds__(" << kCodegenBlock << ", " << min_blocks
           << ") perm_walk(pk::WalkArgs wa, void *xg_base) {\n";
+        o << "    extern __shared__ __align__(16) unsigned char perm_xs[];\n";
         o << "    pk::GenPol pol;\n";
+        o << "    pol.xs = reinterpret_cast<pk::GenPol::X *>(perm_xs) + threadIdx.x;\n";
         o << "    const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
         o << "    pol.stride = (unsigned long long)gridDim.x * blockDim.x;\n";
         o << "    pol.xg = reinterpret_cast<pk::GenPol::X *>(xg_base) + tid;\n";
@@ -487,10 +492,18 @@ struct CacheEntry {
 // A kernel compiled for two resident blocks (128 registers) whose spill
 // frame exceeds this is rebuilt for one block (255 registers).  Dense exact
 // walks (every row in the lowest group, multi-limb products unrolled over the
-// block) are the ones that reach it.  One of them, the 128-bit walk of -J_15
-// with a 1.4 KB frame, returned a wrong top limb, reproducibly and for every
-// chunk size and grid, while the same source built for 255 registers was
-// right; the cause was not found, so the spill-heavy build is not used.
+// block) are the ones that reach it.
+//
+// The 128-bit walk of -J_15 with one ring product per row (1.4 KB of spills at
+// 128 registers) returns a wrong top limb from that build, reproducibly and for
+// every chunk length, while the same source built for 80 or 255 registers is
+// right, and the same source compiled as host C++ under address and
+// undefined-behaviour sanitizers (with automatic variables initialised to zero
+// and to a pattern) matches the CPU oracle chunk by chunk.  The source has no
+// defect those checks can see; the wrong result comes from the device build.
+// So an exact kernel whose 128-register build spills at all (a frame of any
+// size) is also built for 255 registers, both walk the same probe chunks on the
+// GPU, and the 128-register build is kept only if the two agree bit for bit.
 constexpr int kMaxLocalFrame = 512;
 
 std::mutex g_cache_mu;
@@ -498,6 +511,8 @@ std::unordered_map<std::string, CacheEntry> g_cache;
 constexpr size_t kCacheMax = 512;
 
 }  // namespace
+
+bool codegen_no_fold() { return no_fold_env(); }
 
 std::string codegen_source(const perm_plan_s &P) {
     Emitter e(P, codegen_min_blocks(P));
@@ -507,7 +522,7 @@ std::string codegen_source(const perm_plan_s &P) {
 namespace {
 
 // Compiles src with NVRTC for sm_103a and loads it into ce.
-perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::string &err) {
+perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::string &err, size_t smem) {
     Driver &d = driver();
     if (debug_fail(kSiteNvrtc)) { err = "NVRTC compile failed (injected by perm_debug_inject_failures)"; return PERM_ERR_NVRTC; }
     nvrtcProgram prog;
@@ -538,8 +553,74 @@ perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::stri
     if (cr != CUDA_SUCCESS) { err = "cuModuleGetFunction: " + cu_err(cr); return PERM_ERR_CUDA; }
     d.funcGetAttribute(&ce.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ce.function);
     d.funcGetAttribute(&ce.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, ce.function);
-    cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, 0);
+    if (smem > 48 * 1024) {
+        cr = d.funcSetAttribute(ce.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
+        if (cr != CUDA_SUCCESS) { err = "cuFuncSetAttribute: " + cu_err(cr); return PERM_ERR_CUDA; }
+    }
+    cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, smem);
     if (cr != CUDA_SUCCESS) { err = "occupancy: " + cu_err(cr); return PERM_ERR_CUDA; }
+    return PERM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Walks the first chunks of the Gray range (up to 64 warp tasks of 32 chunks
+// of 2^K indices) with two builds of the same exact kernel and compares their
+// per-task partial sums bit for bit.  Uses its own small device buffers and
+// stream.
+perm_status_t same_on_probe(const perm_plan_s &P, const CacheEntry &a, const CacheEntry &b, bool *same,
+                            std::string &err) {
+    Driver &d = driver();
+    const int n = P.m.n;
+    const int K = std::min(n - 1, kCodegenBlockLog2 + 3);
+    const uint64_t chunks = std::min<uint64_t>(P.total >> K, 64 * 32);
+    const uint64_t ntasks = (chunks + 31) / 32;
+    const int words = P.arith;
+    const int grid = (int)std::max<uint64_t>(1, (ntasks + 7) / 8);
+    const size_t ws_words = 16 + ntasks * (size_t)words;
+    const size_t xg_bytes = (size_t)std::max(0, n - P.k - P.k2) * grid * kCodegenBlock * sizeof(int) + 16;
+    unsigned char *buf = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 2 * ws_words * 8 + xg_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    std::vector<uint64_t> out[2];
+    const CacheEntry *k[2] = {&a, &b};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        uint64_t *ws = reinterpret_cast<uint64_t *>(buf) + i * ws_words;
+        e = cudaMemsetAsync(ws, 0, 16 * 8, st);
+        if (e != cudaSuccess) break;
+        pk::WalkArgs wa;
+        wa.chunk_lo = 0;
+        wa.chunk_hi = chunks;
+        wa.ntasks = ntasks;
+        wa.task_counter = reinterpret_cast<unsigned long long *>(ws);
+        wa.task_out = reinterpret_cast<unsigned long long *>(ws + 16);
+        wa.skip_counter = reinterpret_cast<unsigned long long *>(ws + 1);
+        wa.K = K;
+        wa.zero_skip = 1;
+        wa.timeout_ns = 0;
+        wa.deadline_word = reinterpret_cast<unsigned long long *>(ws + 5);
+        wa.abort_flag = reinterpret_cast<unsigned int *>(ws + 6);
+        void *xg = buf + 2 * ws_words * 8;
+        void *params[] = {&wa, &xg};
+        if (d.launchKernel(reinterpret_cast<CUfunction>(k[i]->function), (unsigned)grid, 1, 1, kCodegenBlock, 1, 1,
+                           (unsigned)P.xs_bytes(), reinterpret_cast<CUstream>(st), params, nullptr) != CUDA_SUCCESS) {
+            e = cudaErrorLaunchFailure;
+            break;
+        }
+        out[i].resize(ntasks * (size_t)words);
+        e = cudaMemcpyAsync(out[i].data(), ws + 16, out[i].size() * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (st) cudaStreamDestroy(st);
+    if (buf) cudaFree(buf);
+    if (e != cudaSuccess) {
+        err = std::string("cross-check of two kernel builds: ") + cudaGetErrorString(e);
+        return PERM_ERR_CUDA;
+    }
+    *same = out[0] == out[1];
     return PERM_OK;
 }
 
@@ -568,14 +649,30 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     }
     const double t0 = now_ms();
     CacheEntry ce;
-    perm_status_t st = compile_and_load(src, ce, err);
+    perm_status_t st = compile_and_load(src, ce, err, P.xs_bytes());
     if (st != PERM_OK) return st;
-    if (ce.local_bytes > kMaxLocalFrame && !std::getenv("PERM_CODEGEN_MIN_BLOCKS")) {
+    const bool fixed_budget = std::getenv("PERM_CODEGEN_MIN_BLOCKS") != nullptr;
+    if (ce.local_bytes > kMaxLocalFrame && !fixed_budget) {
         if (driver().moduleUnload) driver().moduleUnload(ce.module);
         ce = CacheEntry();
         Emitter e1(P, 1);
-        st = compile_and_load(e1.emit(), ce, err);
+        st = compile_and_load(e1.emit(), ce, err, P.xs_bytes());
         if (st != PERM_OK) return st;
+    } else if (P.arith != 0 && ce.local_bytes > 0 && !fixed_budget) {
+        // exact kernel with any spills: cross-check against the 255-register build
+        CacheEntry wide;
+        Emitter e1(P, 1);
+        st = compile_and_load(e1.emit(), wide, err, P.xs_bytes());
+        if (st != PERM_OK) { driver().moduleUnload(ce.module); return st; }
+        bool same = false;
+        st = same_on_probe(P, ce, wide, &same, err);
+        if (st != PERM_OK) { driver().moduleUnload(ce.module); driver().moduleUnload(wide.module); return st; }
+        if (same) {
+            driver().moduleUnload(wide.module);
+        } else {
+            driver().moduleUnload(ce.module);
+            ce = wide;
+        }
     }
     P.ms_compile = now_ms() - t0;
     if (use_cache) {
@@ -600,7 +697,8 @@ cudaError_t codegen_launch(perm_plan_s &P, const pk::WalkArgs &wa, cudaStream_t 
     void *xg = P.d_xglob;
     void *params[] = {&a, &xg};
     CUresult r = d.launchKernel(reinterpret_cast<CUfunction>(P.cg.function), (unsigned)P.grid, 1, 1,
-                                (unsigned)P.block, 1, 1, 0, reinterpret_cast<CUstream>(st), params, nullptr);
+                                (unsigned)P.block, 1, 1, (unsigned)P.xs_bytes(), reinterpret_cast<CUstream>(st), params,
+                                nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 

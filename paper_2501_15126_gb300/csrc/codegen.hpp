@@ -39,4 +39,8 @@ cudaError_t codegen_launch(perm_plan_s &P, const pk::WalkArgs &wa, cudaStream_t 
 
 void codegen_release(perm_plan_s &P);
 
+// PERM_CODEGEN_NO_FOLD=1 in the environment: exact generated kernels multiply
+// every row into the ring on its own.
+bool codegen_no_fold();
+
 }  // namespace perm

@@ -447,6 +447,43 @@ double bound_log2(const Matrix &m) {
     return std::min(rows, cols);
 }
 
+double ring_ops_per_step(const Matrix &m, const Layout &L, int limbs, int fold) {
+    const int n = m.n;
+    if (n < 2 || limbs < 2) return 0.0;
+    const double ring = limbs == 2 ? 3.0 : (double)limbs;
+    double rs[kNMax];
+    for (int s = 0; s < n; ++s) {
+        double a = 0.0;
+        for (int j = 0; j < n; ++j) a += std::fabs(m.fval(L.row_order[s], j));
+        rs[s] = std::max(a, 1.0);
+    }
+    double level[kNMax + 1];
+    for (int g = 0; g < n; ++g) {
+        const int b = L.group_begin[g], e = L.group_begin[g + 1];
+        double c = 0.0;
+        int s = b;
+        while (s < e) {
+            int t = s + 1;
+            if (fold == 1) {
+                double bound = rs[s];
+                while (t < e && bound * rs[t] < 2147483647.0) bound *= rs[t++];
+            } else if (fold == 2) {
+                while (t < e && (t & 3) != 0) ++t;   // to the end of the slot quadruple
+            }
+            c += (t - s - 1) + ring;
+            s = t;
+        }
+        level[g] = c;
+    }
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    double total = level[0], prefix = 0.0;
+    for (int j = 1; j <= n - 2; ++j) {
+        prefix += level[j];
+        total += std::ldexp(1.0, n - j - 2) / steps * prefix;
+    }
+    return total;
+}
+
 int abs_shift_for(const Matrix &m) {
     double L = 0.0;
     for (int i = 0; i < m.n; ++i) {

@@ -117,6 +117,16 @@ double cost_per_step_dual(const Layout &L, bool shared_product);
 // (or, for walks long enough for the generated kernels, the cheaper of those
 // and the paired chain); exact: one chain.
 double walk_cost_per_step(const Layout &L, bool fp64);
+// Integer multiply operations per Gray step of an exact walk (the IMAD pipe's
+// work, which bounds it): a ring product of an L-limb value by a 32-bit factor
+// is L wide multiply-adds (3 for L = 2: one 64-bit product), and every extra
+// row folded into a 32-bit product before it is one more multiplication.
+// Level 0 is rebuilt at every step and levels 1..j after a flip of column j
+// (Lemma 2 weights).  fold: 0 = one ring product per row, 1 = runs of a
+// group's rows whose row-sum product stays below 2^31 (generated kernels),
+// 2 = fixed slot quadruples (generic kernels, rows' absolute sums <= 127).
+double ring_ops_per_step(const Matrix &m, const Layout &L, int limbs, int fold);
+
 // The fewest 32-bit limbs (2..6) of a ring that holds 2^(n-1) perm with sign
 // and margin, or 0.
 int exact_limbs_for(double bound, int n);

@@ -63,12 +63,14 @@ struct perm_plan_s {
     size_t img_bytes = 0;     // generic kernels: size of the matrix image
     int K = 0, grid = 1, block = 256, regs = 0;
     int k = 0, c = 0;         // Algorithm 4 split (codegen)
+    int k2 = 0;               // codegen: rows [k, k + k2) of x in shared memory, the rest global
     uint64_t chunk_lo = 0, chunk_hi = 0, ntasks = 0;
     perm::GenericFns gf;
     perm::CodegenKernel cg;
     void *d_devmat = nullptr;
     uint64_t *d_ws = nullptr;   // [0] task counter, [1] skipped blocks, [2..4] result, [8..] task results
     void *d_xglob = nullptr;    // codegen: rows of x kept in global memory
+    size_t xs_bytes() const { return (size_t)k2 * 256 * (arith == 0 ? 8 : 4); }   // per block
     uint64_t *h_res = nullptr;  // pinned copy of d_ws[0..7]
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int computes = 0;                      // perm_compute calls so far

@@ -59,6 +59,39 @@ def combine_exact(words, device="cpu") -> int:
     return total % (1 << (64 * w))
 
 
+def finish_exact(total: int, n: int, words: int) -> int:
+    """The permanent from a whole walk's doubled Nijenhuis-Wilf sum S modulo
+    2^(64 words): S = (-1)^(n-1) 2^(n-1) perm, so the low n-1 bits are zero and
+    the rest is perm with its sign (the library's own finishing step, applied to
+    a sum combined across ranks)."""
+    bits = 64 * words
+    if total & ((1 << (n - 1)) - 1):
+        raise ValueError("combined exact sum is not divisible by 2^(n-1)")
+    v = total >> (n - 1)
+    width = bits - (n - 1)
+    if v >> (width - 1):
+        v -= 1 << width
+    return -v if (n - 1) % 2 else v
+
+
+def permanent_sharded(a, device="cpu", **kw):
+    """One permanent split across the ranks of the default process group:
+    this rank walks its shard of the Gray range on its GPU through the C ABI
+    (perm_plan_create + perm_compute with g_lo/g_hi), then one all_gather of
+    the partial sums and the finishing step give every rank the same value.
+    Returns (value, this rank's Result)."""
+    from paper_2501_15126_gb300 import _abi as A
+    n = a.shape[0]
+    lo, hi = shard_range(1 << (n - 1), dist.get_world_size(), dist.get_rank())
+    r = A.permanent(a, g_lo=lo, g_hi=hi, **kw)
+    if r.vtype == A.PERM_I64:
+        words = [int(r.partial[i]) for i in range(r.exact_words)]
+        return finish_exact(combine_exact(words, device), n, r.exact_words), r
+    s_hi, s_lo = combine_f64(r.f64, r.f64_lo, device)
+    f = 2.0 if n % 2 else -2.0          # 4 (n mod 2) - 2, Algorithm 1
+    return (s_hi + s_lo) * f, r
+
+
 def max_over_ranks(value: float, device="cpu") -> float:
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)

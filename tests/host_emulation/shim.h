@@ -15,7 +15,8 @@
 #define __global__
 #define __forceinline__ inline
 #define __launch_bounds__(...)
-#define __shared__ static
+#define __shared__
+#define __align__(n) __attribute__((aligned(n)))
 
 using std::fma;
 using std::max;

@@ -27,15 +27,17 @@ U = 2.0 ** -53
 
 HARNESS = r'''
 #include "shim.h"
+alignas(16) unsigned char perm_xs[16];   // the kernel's dynamic shared memory (unused: the harness sets pol.xs)
 #include "walk.cu"
 #include <cstdio>
 #include <cstdlib>
 int main(int argc, char **argv) {
     const int K = std::atoi(argv[1]);
-    static pk::GenPol::X xg[64];
+    static pk::GenPol::X xg[64], xs[64 * 256];
     pk::GenPol pol;
     pol.xg = xg;
     pol.stride = 1;
+    pol.xs = xs;
     unsigned long long q;
     while (std::scanf("%llu", &q) == 1) {
         unsigned long long skipped = 0, w[6] = {0, 0, 0, 0, 0, 0};
@@ -139,6 +141,7 @@ def test_band_plus_off_band_exact_with_global_rows():
     K = 9
     top = (1 << 47) >> K
     check_exact(a, K, [0, 5, top // 3, top - 1], reg_rows=20)
+    check_exact(a, K, [0, top // 5, top - 1], reg_rows=20, shared_rows=12)   # three tiers
 
 
 @pytest.mark.parametrize("flags", [0, 4])

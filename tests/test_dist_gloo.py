@@ -83,3 +83,61 @@ def test_shard_range_covers_exactly():
                 assert b == c
             for a, b in shards[:-1]:
                 assert a % 32 == 0 and b % 32 == 0
+
+
+def test_finish_exact_matches_the_oracle_finishing():
+    """The host-side finishing of a combined exact sum (Algorithm 1 with doubled
+    x: S = (-1)^(n-1) 2^(n-1) perm modulo 2^(64 w)) against Eq. 2."""
+    import oracle
+    from paper_2501_15126_gb300 import dist as pd
+    from paper_2501_15126_gb300 import synth
+    for n, seed in ((9, 1), (14, 2), (17, 3)):
+        a = synth.single_er(n, 0.4, seed, values="01")
+        a[0, :] *= -1 if seed == 2 else 1
+        s = oracle.nw2_range(a, 0, 1 << (n - 1))
+        assert pd.finish_exact(s, n, 2) == oracle.ryser_gray(a)
+
+
+def gpu_shard_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2501_15126_gb300 import dist as pd
+        from paper_2501_15126_gb300 import synth
+        af = synth.single_er(24, 0.25, 19, values="f64")
+        ai = synth.single_er(24, 0.25, 19, values="01")
+        vf, rf = pd.permanent_sharded(af)
+        vi, ri = pd.permanent_sharded(ai)
+        q.put((rank, vf, vi, rf.steps, ri.steps))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_two_processes_shard_one_permanent_through_the_c_abi():
+    """Two processes (sharing the one GPU; their kernels never wait on each
+    other) each walk half of the Gray range of one n=24 permanent through
+    perm_plan_create + perm_compute; the partial sums are combined over gloo.
+    FP64 within 1e-9 of the oracle, exact bit-identical to Eq. 2."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=gpu_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=600) for _ in range(2))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    import oracle
+    from paper_2501_15126_gb300 import synth
+    af = synth.single_er(24, 0.25, 19, values="f64")
+    ai = synth.single_er(24, 0.25, 19, values="01")
+    want_f = float(oracle.nw_perm(af, threads=8)[0])
+    want_i = oracle.ryser_gray(ai)
+    for r in out:
+        assert abs(r[1] - want_f) <= 1e-9 * abs(want_f)
+        assert r[2] == want_i
+        assert r[3] == r[4] == 1 << 22

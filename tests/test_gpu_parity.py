@@ -251,6 +251,22 @@ def test_cfg3_subranges_exact_and_f64():
     subrange_check_exact(a01, 1 << 30, (1 << 30) + span, engine=A.PERM_ENGINE_GENERIC)
 
 
+def test_three_level_placement_registers_shared_global():
+    """The n=48 band workload with x in three tiers (Sec. V's split, carried to
+    shared memory as Sec. VIII proposes): 20 rows in registers, 12 or 28 in
+    shared memory, the rest in global memory; sub-ranges with high Gray bits
+    set against the oracle, exact and FP64."""
+    a01 = synth.band_plus(48, 3, 2, seed=3, values="01")
+    af = synth.band_plus(48, 3, 2, seed=3, values="f64")
+    span = 1 << 20
+    for lo in (0, (1 << 46) + (5 << 33)):
+        for k2 in (12, 28):
+            kw = dict(engine=A.PERM_ENGINE_CODEGEN, reg_rows=20, shared_rows=k2)
+            subrange_check_exact(a01, lo, lo + span, **kw)
+            subrange_check_f64(af, lo, lo + span, **kw)
+            assert A.permanent(a01, g_lo=lo, g_hi=lo + span, **kw).shared_rows == k2
+
+
 @pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
 def test_band_only_sibling_full_walk_against_band_dp(engine):
     """Band-only matrices (|i-j| <= 3, no off-band entries) walked in full on the

@@ -225,3 +225,18 @@ def test_generated_exact_kernels_built_for_128_registers():
             assert r.value == want, (a.shape, w)
     finally:
         del os.environ["PERM_CODEGEN_MIN_BLOCKS"]
+
+
+def test_spilling_exact_kernels_are_checked_against_the_wide_build(monkeypatch):
+    """At the default register budget an exact generated kernel whose
+    128-register build spills is either rebuilt for 255 registers (frames above
+    512 bytes: -J_15 with one ring product per row) or cross-checked against
+    that build on probe chunks (J_30 in a 192-bit ring); both give their closed
+    forms."""
+    monkeypatch.delenv("PERM_CODEGEN_MIN_BLOCKS", raising=False)
+    monkeypatch.setenv("PERM_CODEGEN_NO_FOLD", "1")
+    r = A.permanent(-synth.ones(15), engine=CG, exact_words=2, flags=A.PERM_FLAG_NO_KERNEL_CACHE)
+    assert r.value == -math.factorial(15)
+    monkeypatch.delenv("PERM_CODEGEN_NO_FOLD")
+    r = A.permanent(synth.ones(30), engine=CG, exact_words=3, flags=A.PERM_FLAG_NO_KERNEL_CACHE)
+    assert r.value == math.factorial(30)
