@@ -536,6 +536,8 @@ def measure_serving(A, rate=2000.0, duration=60.0, sequential_seconds=10.0, accu
            "perms_per_s": len(reqs) / wall, "requests": len(reqs), "seconds": wall,
            "p50_ms": q(lat, 50), "p99_ms": q(lat, 99), "max_ms": q(lat, 100),
            "failed": sum(1 for r in res if r.status != 0),
+           "max_ms_by_n": {str(n): round(max(l for l, rq in zip(lat, reqs) if rq.a.shape[0] == n) * 1e3, 2)
+                           for n in sorted({rq.a.shape[0] for rq in reqs})},
            "double_double_reruns": sum(1 for r in res if r.precision == 2),
            "workload": "Poisson arrivals at %g req/s for %g s, n = 16 + m with P(m) ~ 2^-m up to 40, p uniform in "
                        "[0.1,0.3] + diagonal, mixed 0/1 and (0,1], seed 5" % (rate, duration),
@@ -683,7 +685,8 @@ def run_profile_case(args):
     n = a.shape[0]
     # a prefix of the walk, or (when it covers the range) the whole walk with its own ring width
     g_hi = 0 if args.profile_log2 >= n - 1 else 1 << args.profile_log2
-    p = A.Plan(a, g_lo=0, g_hi=g_hi, engine=engine, flags=A.PERM_FLAG_PAIRED_CHAIN if args.profile_paired else 0)
+    p = A.Plan(a, g_lo=0, g_hi=g_hi, engine=engine, flags=A.PERM_FLAG_PAIRED_CHAIN if args.profile_paired else 0,
+               chunk_log2=args.profile_chunk_log2)
     for _ in range(args.steps):
         r = p.compute()
     print(json.dumps({"profile_case": vals, "matrix": args.profile_matrix, "n": n, "engine": args.profile_engine,
@@ -713,6 +716,7 @@ def main():
     ap.add_argument("--max-slices", type=int, default=0, help="cfg3: slices per run per call (0 = all)")
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
+    ap.add_argument("--profile-chunk-log2", type=int, default=0, help="profile: K (0 = the plan's choice)")
     ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
     ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28", "band48"],
                     help="bench: the n=36 bench matrix (the n=48 band with --profile-exact); "

@@ -114,7 +114,7 @@ enum {
    sum_g |term_g|, at several times the FP64 cost. */
 enum {
     PERM_PREC_AUTO = 0,  /* FP64; a whole walk of n <= 32 whose estimate n 2^-53 sum|terms| / |perm|  */
-                         /*   exceeds 1e-10 (or whose FP64 result is 0) is rerun in double-double      */
+                         /*   exceeds 1e-9 (or whose FP64 result is 0) is rerun in double-double       */
     PERM_PREC_F64 = 1,   /* FP64 only                                                                */
     PERM_PREC_DD = 2     /* double-double (generic kernels, n <= 48)                                  */
 };
