@@ -363,16 +363,18 @@ Layout choose_layout(const Matrix &m, int ordering_opt) {
     order_degree(m, cols);
     Layout deg = make_layout(m, cols, PERM_ORDER_DEGREE);
     Layout start = cost_per_step(deg, false) < cost_per_step(paper, false) ? deg : paper;
-    // AUTO / SEARCH: for FP64 walks of 2^30 steps and more (the generated
-    // kernels' range), refine the better order under the model of the scheme
-    // the walk will run.  The search takes about 0.2 ms of host time at
-    // n = 28, more than shorter walks would gain; exact kernels fold runs of
-    // rows in 32 bits, which the one-chain model does not see (a searched
-    // order made the n=48 band's exact walk 7 % slower), so they keep the
-    // start order.
-    if (m.n < 31 || m.is_int) return start;
+    // AUTO / SEARCH: for FP64 walks of 2^21 steps and more, refine the better
+    // order under the model of the scheme the walk will run (two-state chains
+    // below n = 31, where the generic kernels run; the cheaper of those and the
+    // paired chain from n = 31, the generated kernels' range).  The search
+    // takes about 0.1-0.2 ms of host time at n = 22..28 and cuts the counted
+    // FP64 operations of the batch workload's matrices there by 15-16 % (its
+    // FP64 half: 2.15 s -> 1.76 s).  Exact kernels fold runs of rows in 32
+    // bits, which the one-chain model does not see (a searched order made the
+    // n=48 band's exact walk 7 % slower), so they keep the start order.
+    if (m.n < 22 || m.is_int) return start;
     for (int p = 0; p < m.n; ++p) cols[p] = start.col_order[p];
-    const bool fp64 = true, long_walk = true;
+    const bool fp64 = true, long_walk = m.n >= 31;
     const double before = order_cost(m, cols, fp64, long_walk);
     search_order(m, cols, fp64, long_walk);
     if (!(order_cost(m, cols, fp64, long_walk) < before - 1e-12)) return start;
