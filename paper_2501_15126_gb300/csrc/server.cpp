@@ -15,7 +15,9 @@
 //              the oldest requests, so large requests progress in slices
 //              while small ones that arrive meanwhile are not held back;
 //              waves alternate between two streams, so a new wave overlaps
-//              the tail of the previous one on the device;
+//              the tail of the previous one on the device; image uploads and
+//              final reductions go on a third stream, so neither waits behind
+//              a wave;
 //   results    each task writes its sum to a fixed place in the request's own
 //              result range, whatever wave ran it; when all of a request's
 //              waves are done one fixed-order reduction produces its value.
@@ -47,7 +49,7 @@ namespace perm {
 
 namespace {
 
-constexpr int kStreams = 2;
+constexpr int kStreams = 2;                   // wave streams; one more (aux) takes uploads and reductions
 constexpr uint64_t kSmallShare = 64;          // tasks every active request gets per wave
 constexpr double kWaveSteps = 268435456.0;    // Gray steps per wave (2^28, a few ms): short waves let
                                               // requests that arrive meanwhile start soon
@@ -158,6 +160,7 @@ struct perm_server_s {
     std::unordered_map<uint64_t, perm_result_t> results;  // finished, not yet polled
     std::vector<Family> fam;
     cudaStream_t streams[kStreams] = {};
+    cudaStream_t aux = nullptr;   // image uploads and final reductions, never queued behind a wave
     static constexpr int kWaves = 4, kFinishes = 4;
     Wave waves[kWaves];
     Finish finishes[kFinishes];
@@ -173,6 +176,8 @@ struct perm_server_s {
     perm_status_t init_device() {
         cudaError_t e = cudaSetDevice(device);
         if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+        if ((e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
         for (int i = 0; i < kStreams; ++i)
             if ((e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamCreate");
@@ -245,6 +250,7 @@ struct perm_server_s {
         }
         for (int i = 0; i < kStreams; ++i)
             if (streams[i]) cudaStreamDestroy(streams[i]);
+        if (aux) cudaStreamDestroy(aux);
     }
 
     // ---- called with mu held
@@ -287,13 +293,13 @@ struct perm_server_s {
             P.nmax = F.nmax;
             r->ntasks = ntasks;
             r->out_offset = off;
-            // the image goes up on stream 0 before any wave that reads it
+            // the image goes up on the aux stream; every wave waits for the uploads made so far
             std::vector<unsigned char> img;
             build_devmat(P.m, P.L, F.img, F.nmax, img);
             r->img_bytes = img.size();
             const cudaError_t e = debug_fail(kSiteUpload) ? cudaErrorInvalidValue
                                   : cudaMemcpyAsync(F.d_images + (size_t)r->slot * F.gf.devmat_bytes, img.data(),
-                                                    img.size(), cudaMemcpyHostToDevice, streams[0]);
+                                                    img.size(), cudaMemcpyHostToDevice, aux);
             if (e != cudaSuccess) fail_request(r, cuda_fail(e, "serving: image upload"));
         }
         steps_active += steps;
@@ -449,7 +455,7 @@ struct perm_server_s {
                 f->h_seg[2 * i + 1] = f->reqs[i]->ntasks;
             }
             f->family = fi;
-            cudaStream_t st = streams[0];
+            cudaStream_t st = aux;   // its requests' waves are done (their events were seen)
             cudaError_t e = cudaMemcpyAsync(f->d_seg, f->h_seg, 16 * cnt, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess)
                 e = debug_fail(kSiteFinish) ? cudaErrorLaunchFailure
@@ -533,7 +539,7 @@ struct perm_server_s {
         while (true) {
             if (stop) break;
             admit();
-            cudaEventRecord(upload_done, streams[0]);
+            cudaEventRecord(upload_done, aux);   // waves wait for the uploads only
             // requests that run their own plan
             for (size_t i = 0; i < active.size(); ++i) {
                 Request *r = active[i];
@@ -647,6 +653,7 @@ struct perm_server_s {
         // shutdown: drain the device, cancel what is left
         lk.unlock();
         for (int i = 0; i < kStreams; ++i) cudaStreamSynchronize(streams[i]);
+        cudaStreamSynchronize(aux);
         lk.lock();
         perm_result_t res;
         std::memset(&res, 0, sizeof(res));
