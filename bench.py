@@ -188,8 +188,8 @@ def cpu_fp64_baseline(a, seconds_hint: float = 10.0):
         k += 1
         dt = run(1 << k)
     return {"value": (1 << k) / dt, "unit": "steps/s", "cores": cores, "kind": "cpu-sparseperman (FP64)",
-            "sample": "Gray indices [0, 2^%d) of the n=36 matrix: FP64 Algorithm 1, degree-sorted columns, zero "
-                      "tracking, %d threads over aligned 2^%d-step chunks" % (k, cores, K),
+            "sample": "Gray indices [0, 2^%d) of the n=%d matrix: FP64 Algorithm 1, degree-sorted columns, zero "
+                      "tracking, %d threads over aligned 2^%d-step chunks" % (k, n, cores, K),
             "seconds": dt, "ms_per_permanent_extrapolated": 1e3 * dt * (1 << (n - 1 - k))}
 
 
@@ -687,6 +687,75 @@ def run_ablation(args):
     return 0
 
 
+# Table III: CodeGen-Hybrid on the real matrices, seconds on an A100 (the paper's numbers; other
+# matrices with these shapes and another GPU: context only)
+PAPER_TABLE3_HYBRID_S = {"bcsstk01": 882.94, "mycielskian6": 477.75, "mesh1e1": 860.19, "d_ss": 21448.17,
+                         "curtis54": 47841.18, "bcspwr02": 1317.42}
+
+
+def zero_product_fraction(a, samples=1 << 16, seed=11):
+    """Fraction of the 2^(n-1) Gray-walk terms whose product has a zero factor,
+    estimated from uniformly drawn column subsets (host, numpy)."""
+    n = a.shape[0]
+    a = a.astype(np.float64)
+    x0 = a[:, n - 1] - 0.5 * a.sum(axis=1)
+    g = np.random.default_rng(seed)
+    S = (g.random((samples, n - 1)) < 0.5).astype(np.float64)
+    return float(((x0[None, :] + S @ a[:, : n - 1].T) == 0).any(axis=1).mean())
+
+
+def run_table2(args, seconds_per_range=0.25):
+    """Matrices with the shapes of the paper's real-life set (Table II; values
+    as Sec. VI-E describes them): the library's default plan timed by CUDA
+    events on four Gray sub-ranges spread over the walk (their sizes picked
+    for about `seconds_per_range` each), the fraction of blocks the zero skip
+    removed, the fraction of zero products (host sample), the projected time
+    of the whole walk, and CPU-SparsePerman (FP64, zero tracking) on a prefix."""
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    from paper_2501_15126_gb300 import synth
+    torch.cuda.set_device(0)
+    out = {"workload": "table2", "note": "random matrices with Table II's n, nnz, symmetry and value structure "
+                                         "(not the SuiteSparse matrices)", "matrices": {}}
+    for sh in synth.TABLE2_SHAPES:
+        a = synth.table2_like(sh.name)
+        n = a.shape[0]
+        top = 1 << (n - 1)
+        p = A.Plan(a, g_lo=0, g_hi=1 << 30)
+        p.compute()
+        r = p.compute()
+        p.close()
+        k = int(np.clip(np.floor(np.log2(max(r.steps / (r.ms_kernel / 1e3), 1.0) * seconds_per_range)), 30, n - 3))
+        ms, steps, skipped, first = 0.0, 0, 0.0, None
+        for i in range(4):
+            lo = (i * (top >> 2)) >> k << k
+            p = A.Plan(a, g_lo=lo, g_hi=lo + (1 << k))
+            p.compute()
+            r = p.compute()
+            p.close()
+            first = first or r
+            ms += r.ms_kernel
+            steps += r.steps
+            skipped += r.zero_skip_frac * r.steps
+        rate = steps / (ms / 1e3)
+        cpu = cpu_fp64_baseline(a.astype(np.float64), seconds_hint=2.0)
+        rec = {"n": n, "nnz": int(np.count_nonzero(a)), "values": sh.values,
+               "arithmetic": "exact (%d-bit ring)" % (64 * first.exact_words) if first.vtype == A.PERM_I64 else "fp64",
+               "engine": "codegen" if first.engine == A.PERM_ENGINE_CODEGEN else "generic",
+               "regs": first.regs_per_thread, "chunk_log2": first.chunk_log2,
+               "ranges": "4 x 2^%d steps at 0, 1/4, 1/2, 3/4 of the walk" % k,
+               "gray_steps_per_s": rate, "zero_skip_frac": skipped / steps,
+               "zero_product_frac": zero_product_fraction(a),
+               "projected_whole_walk_s": top / rate,
+               "paper_table3_hybrid_s_a100_real_matrix": PAPER_TABLE3_HYBRID_S[sh.name],
+               "cpu_sparseperman_fp64_steps_per_s": cpu["value"], "cpu_cores": cpu["cores"],
+               "gpu_over_cpu": rate / cpu["value"]}
+        out["matrices"][sh.name] = rec
+        print(json.dumps({sh.name: rec}), flush=True)
+    print(json.dumps(out))
+    return 0
+
+
 def run_profile_case(args):
     """A small case of the bench kernel for `ncu --set full`: the same matrix,
     plan and generated kernel, walking only the Gray sub-range [0, 2^k)."""
@@ -731,7 +800,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="single workload: only the headline (no batch, serving, accuracy, cold e2e, FP64 CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile", "cfg3", "ablation"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile", "cfg3", "ablation",
+                                                             "table2"])
     ap.add_argument("--ckpt-dir", default="gpurun_out/cfg3_ckpt", help="cfg3: checkpoint files")
     ap.add_argument("--slice-log2", type=int, default=40, help="cfg3: Gray indices per checkpointed slice (log2)")
     ap.add_argument("--max-slices", type=int, default=0, help="cfg3: slices per run per call (0 = all)")
@@ -760,6 +830,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "cfg3":
         return run_cfg3(args)
+    if args.workload == "table2":
+        return run_table2(args)
     if args.workload == "ablation":
         return run_ablation(args)
     return run_ours(args)

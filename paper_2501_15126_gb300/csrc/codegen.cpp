@@ -294,6 +294,24 @@ struct Emitter {
         } else if (!P.pure_reg) {
             for (int g : hi) o << "    P Q" << g << ";\n";
         }
+        // level L >= B of the chain(s) is zero: the stored level at the first
+        // nonempty group >= L (the zero spans of core.cuh)
+        o << "    __device__ __forceinline__ bool level_zero(int L) const {\n";
+        if (!P.pure_reg) {
+            o << "        switch (L) {\n";
+            for (int L = B; L < n; ++L) {
+                int g = -1;
+                for (int h = L; h < n && g < 0; ++h)
+                    if (P.dual ? level_nonempty(h) : P.L.group_begin[h + 1] > P.L.group_begin[h]) g = h;
+                if (g < 0) continue;
+                if (P.dual)
+                    o << "        case " << L << ": return A::is_zero(QA" << g << ") && A::is_zero(QB" << g << ");\n";
+                else
+                    o << "        case " << L << ": return A::is_zero(Q" << g << ");\n";
+            }
+            o << "        default: break;\n        }\n";
+        }
+        o << "        return false;\n    }\n";
         // flips inside the unrolled block (static column, static or runtime sign)
         o << "    template <int J, int S> __device__ __forceinline__ void flip(X (&x)[NX]) {\n";
         for (int p = 0; p < B && p < n - 1; ++p) {

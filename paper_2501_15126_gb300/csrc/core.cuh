@@ -42,9 +42,18 @@
 // permanent ordering of Algorithm 3 the low levels hold few rows.  Every term
 // is still the product of the same n numbers; only the association changes.
 //
-// Zero skip (Sec. VI-B's zero tracking, made warp-uniform).  When Q_B is zero
-// in every lane at a block boundary, all 2^B products of the block are zero:
-// the block is replaced by its net effect on x (one flip of column B-1).
+// Zero skip (Sec. VI-B's zero tracking, made warp-uniform; Sec. VI-E and
+// Sec. VIII: repeated values make zero entries of x persist).  When Q_B is
+// zero in every lane at a block boundary, all 2^B products of the block are
+// zero: the block is replaced by its net effect on x (one flip of column
+// B-1).  The skip then widens level by level: blocks h .. h+2^m-1, with h a
+// multiple of 2^m, flip only columns below B+m, so Q_{B+m} is constant over
+// them, and where it is zero in every lane the whole aligned span of 2^(B+m)
+// steps is zero.  Over an aligned span of 2^(B+m) Gray indices every column
+// below B+m-1 flips an even number of times and column B+m-1 once, at the
+// middle index (sign by bit B+m of the span's start, Theorem 1), so the span's
+// net effect on x is that one flip.  Levels B..B+m-1 go stale; the flip at
+// the next block boundary is of a column >= B+m and rebuilds them.
 #pragma once
 
 #include "devmat.h"
@@ -66,6 +75,13 @@ __device__ __forceinline__ u64 warp_or64(u64 v) {
     const u32 lo = __reduce_or_sync(PERM_FULLMASK, (u32)v);
     const u32 hi = __reduce_or_sync(PERM_FULLMASK, (u32)(v >> 32));
     return ((u64)hi << 32) | lo;
+}
+
+// Sum of a 64-bit value over the 32 lanes of a (converged) warp, in every lane.
+__device__ __forceinline__ u64 warp_sum64(u64 v) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(PERM_FULLMASK, v, d);
+    return v;
 }
 
 // Nanoseconds from the GPU's global timer (0 when the walk code runs as
@@ -497,6 +513,20 @@ struct PairSteps {
     }
 };
 
+// ------------------------------------------------------------------ zero spans
+// At block h of a chunk of 2^K steps whose block products are all zero (every
+// lane), the largest m such that the aligned span of blocks h .. h+2^m-1 is
+// all zero too: m <= ctz(h) (the whole chunk at h = 0), and Q_{B+m} zero in
+// every lane.  Zero levels are nested (Q_{B+m} is Q_{B+m+1} times more rows),
+// so the search climbs until a level is nonzero in some lane.
+template <class Pol, int Bv>
+__device__ __forceinline__ int zero_span(const Pol &pol, u64 h, int K) {
+    const int t = h ? ctz64(h) : K - Bv;
+    int m = 0;
+    while (m < t && __all_sync(PERM_FULLMASK, pol.level_zero(Bv + m + 1))) ++m;
+    return m;
+}
+
 // ------------------------------------------------------------------ two-state chains
 // Policies with kDual never apply column 0 to x.  A step's product is
 //     prod_i x_i = (column 0 off) ? A_1 : B_1,
@@ -600,8 +630,11 @@ __device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int 
         // the vote is also the warp's reconvergence point (see walk_chunk_single)
         const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(QA) && A::is_zero(QB));
         if (zero_skip && all_zero) {
-            pol.template flip_rt<Bv - 1>(x, s_mid);
-            ++skipped;
+            const int m = zero_span<Pol, Bv>(pol, h, K);
+            if (m == 0) pol.template flip_rt<Bv - 1>(x, s_mid);
+            else pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
+            skipped += 1ull << m;
+            h += (1ull << m) - 1;
             continue;
         }
         P LA[Bv + 1], LB[Bv + 1];
@@ -651,9 +684,13 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
         // the warp reconverges after the data-driven loops of a flip.
         const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(QB));
         if (zero_skip && all_zero) {
-            // every product of this block is zero; apply the block's net flip
-            pol.template flip_rt<Bv - 1>(x, s_mid);
-            ++skipped;
+            // every product of this block (and of the widest zero span that
+            // starts here) is zero; apply the span's net flip
+            const int m = zero_span<Pol, Bv>(pol, h, K);
+            if (m == 0) pol.template flip_rt<Bv - 1>(x, s_mid);
+            else pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
+            skipped += 1ull << m;
+            h += (1ull << m) - 1;
             continue;
         }
         P Q[Bv + 1];
@@ -698,12 +735,18 @@ __device__ __forceinline__ void walk_tasks(Pol &pol, const WalkArgs &wa) {
         u64 q = wa.chunk_lo + task * 32ull + (u64)lane;
         const bool live = q < wa.chunk_hi;
         if (!live) q = wa.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
+        const u64 skipped_before = skipped;
         typename A::Acc acc = walk_chunk<Pol, A, Bv>(pol, q, wa.K, wa.zero_skip, skipped);
-        if (!live) acc = A::acc_zero();
+        if (!live) {
+            acc = A::acc_zero();
+            skipped = skipped_before;
+        }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
         if (lane == 0) A::acc_store(wa.task_out + task * (u64)A::ACC_WORDS, acc);
     }
+    // every lane counts its own skipped blocks (of live chunks)
+    skipped = warp_sum64(skipped);
     if (wa.skip_counter && lane == 0 && skipped) atomicAdd(wa.skip_counter, skipped);
 }
 

@@ -342,6 +342,12 @@ struct GenericPol {
         QB = qb;
     }
 
+    // level L >= B of the chain(s) is zero (both chains for the two-state walk)
+    __device__ __forceinline__ bool level_zero(int L) const {
+        if constexpr (kDual) return A::is_zero(Qh[L]) && A::is_zero(Bh[L]);
+        else return A::is_zero(Qh[L]);
+    }
+
     // x = x0 + sum of the columns set in Gray code G (columns < n-1 only);
     // called by the whole warp, which visits the union of its lanes' columns
     __device__ __forceinline__ void init_x(X (&x)[NX], u64 G) {
@@ -397,8 +403,12 @@ __device__ __forceinline__ typename A::Acc walk_chunk_compact(GenericPol<NMAX, A
         // data-driven loops of the flips
         const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(qB));
         if (zero_skip && all_zero) {
-            pol.flip_dyn(Bv - 1, x, s_mid);   // the block's net effect on x
-            ++skipped;
+            // the widest all-zero span that starts here (core.cuh: zero_span)
+            // and its net effect on x
+            const int m = zero_span<GenericPol<NMAX, A>, Bv>(pol, h, K);
+            pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
+            skipped += 1ull << m;
+            h += (1ull << m) - 1;
             continue;
         }
         typename A::Blk blk = A::blk_zero();
@@ -461,16 +471,22 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
         const bool live = q < bm.chunk_hi;
         if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
         GenericPol<NMAX, A> pol(slot, bm.abs_shift);
+        const u64 skipped_before = skipped;
         typename A::Acc acc;
         if constexpr (GenericPol<NMAX, A>::kDual)
             acc = walk_chunk_dual<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
         else
             acc = walk_chunk_compact<NMAX, A>(pol, q, bm.K, ba.zero_skip, skipped);
-        if (!live) acc = A::acc_zero();
+        if (!live) {
+            acc = A::acc_zero();
+            skipped = skipped_before;
+        }
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
         if (lane == 0) A::acc_store(ba.task_out + (bm.out_offset + (task - bm.task_begin)) * (u64)A::ACC_WORDS, acc);
     }
+    // every lane counts its own skipped blocks (of live chunks)
+    skipped = warp_sum64(skipped);
     if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
 }
 

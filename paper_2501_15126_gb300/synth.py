@@ -22,6 +22,11 @@ matching excluded) and the five workloads this library is measured on:
 * ``serving_stream`` Poisson arrivals with n = 16 + m, P(m) proportional to
                     2^-m for m = 0..24, p uniform in [0.1, 0.3], forced
                     diagonal, value type a fair coin.
+* ``table2_like``   six matrices with the shapes of the real-life set of
+                    Table II (n, nnz, symmetric or not, diagonal or not) and
+                    the value structure Sec. VI-E describes for them (mostly
+                    distinct reals; all ones; over half +-1 with 40 distinct
+                    values).  Patterns are random, not the real matrices.
 
 Real values are (u + 1) * 2^-53 with u uniform on [0, 2^53): exactly
 representable doubles in (0, 1].
@@ -91,6 +96,74 @@ def band_plus(n: int = 48, w: int = 3, extra: int = 2, seed: int = 3, values: st
             off = np.flatnonzero(np.abs(idx - i) > w)
             pat[i, g.choice(off, size=extra, replace=False)] = True
     return np.ascontiguousarray(fill_values(g, pat, values))
+
+
+@dataclass(frozen=True)
+class Table2Shape:
+    name: str              # the Table II matrix whose shape this copies
+    n: int
+    nnz: int
+    symmetric: bool        # symmetric pattern (and values)
+    diagonal: bool         # every diagonal entry present
+    values: str            # "real": distinct (0,1] reals; "01": all ones; "pm1": > half +-1, 40 distinct
+
+
+# Table II: name, n, nnz; the pattern kind and values follow Sec. VI-E's description of each matrix
+# (stiffness, graph, mesh, power network, CFD, and d_ss's repeated +-1 values).
+TABLE2_SHAPES = (
+    Table2Shape("bcsstk01", 48, 400, True, True, "real"),
+    Table2Shape("mycielskian6", 47, 472, True, False, "01"),
+    Table2Shape("mesh1e1", 48, 306, True, True, "real"),
+    Table2Shape("bcspwr02", 49, 167, True, True, "01"),
+    Table2Shape("curtis54", 54, 291, False, True, "01"),
+    Table2Shape("d_ss", 53, 144, False, True, "pm1"),
+)
+
+
+def table2_like(name: str, seed: int = 7) -> np.ndarray:
+    """A random matrix with the shape of Table II's matrix ``name``: n, nnz,
+    symmetry and diagonal as listed, values as Sec. VI-E describes them.  A
+    pattern without a diagonal gets a random Hamiltonian cycle first, so it
+    always has a perfect matching.  int64 for 0/1 values, float64 otherwise."""
+    sh = next(t for t in TABLE2_SHAPES if t.name == name)
+    g = rng(seed + 1000 * TABLE2_SHAPES.index(sh))
+    n = sh.n
+    pat = np.zeros((n, n), dtype=bool)
+    if sh.diagonal:
+        np.fill_diagonal(pat, True)
+    else:
+        cyc = g.permutation(n)
+        for k in range(n):
+            i, j = cyc[k], cyc[(k + 1) % n]
+            pat[i, j] = pat[j, i] = True
+    off = np.flatnonzero(~np.eye(n, dtype=bool).ravel())
+    while int(pat.sum()) < sh.nnz:
+        i, j = divmod(int(g.choice(off)), n)
+        if pat[i, j]:
+            continue
+        if sh.symmetric:
+            if int(pat.sum()) + 2 > sh.nnz:
+                raise ValueError("a symmetric pattern needs an even off-diagonal count")
+            pat[i, j] = pat[j, i] = True
+        else:
+            pat[i, j] = True
+    if sh.values == "01":
+        return pat.astype(np.int64)
+    a = np.zeros((n, n), dtype=np.float64)
+    if sh.values == "real":
+        vals = unit_values(g, sh.nnz)
+    else:   # "pm1": 55 % of the entries +1 or -1, the rest from 38 other distinct values
+        pool = np.concatenate([[1.0, -1.0], np.round(g.uniform(-4.0, 4.0, 38), 3)])
+        k1 = int(round(0.55 * sh.nnz))
+        vals = np.concatenate([g.choice(pool[:2], k1), pool[2:], g.choice(pool[2:], sh.nnz - k1 - 38)])
+        vals = vals[g.permutation(sh.nnz)]
+    if sh.symmetric:
+        iu = np.argwhere(np.triu(pat))
+        for (i, j), v in zip(iu, vals):
+            a[i, j] = a[j, i] = v
+    else:
+        a[pat] = vals
+    return np.ascontiguousarray(a)
 
 
 @dataclass

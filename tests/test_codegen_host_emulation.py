@@ -151,3 +151,25 @@ def test_generated_f64_walks(flags):
     of the oracle's, and their sums of |terms| within 1e-4."""
     a = synth.single_er(24, 0.2, 1, values="f64")
     check_f64(a, 9, [0, 3, 1000, (1 << 23 >> 9) - 1], flags=flags)
+
+
+@pytest.mark.parametrize("name", ["curtis54", "bcspwr02"])
+def test_zero_spans_on_binary_table2_shapes(name):
+    """Binary matrices with Table II's shapes, where almost every product is
+    zero (Sec. VI-E): the walk skips whole aligned spans of blocks (up to a
+    whole 2^12-step chunk) and applies each span's net flip.  Every chunk's
+    sum must still equal the oracle's over the same Gray range."""
+    a = synth.table2_like(name)
+    K = 12
+    top = (1 << (a.shape[0] - 1)) >> K
+    check_exact(a, K, [0, 1, 2, 3, top // 7, top // 3 + 1, top - 2, top - 1])
+
+
+def test_zero_spans_on_the_d_ss_shape_in_fp64():
+    """The d_ss shape (over half of the values +-1, 40 distinct): FP64 walk
+    (with the sum of |terms|, which a walk of n > 32 keeps only on request),
+    chunk sums within the rounding bound of the oracle's."""
+    a = synth.table2_like("d_ss")
+    K = 12
+    top = (1 << (a.shape[0] - 1)) >> K
+    check_f64(a, K, [0, 5, top // 3, top - 1], flags=A.PERM_FLAG_ABS_SUM)
