@@ -16,6 +16,8 @@ paper's definitions:
 * ``nw_perm``          Algorithm 1 over the whole range times (4 (n mod 2) - 2).
 * ``nw2_range``        Algorithm 1 with doubled x, in integers modulo 2^128.
 * ``band_dp``          row-by-row dynamic program for banded matrices (independent of Ryser).
+* ``rowdp``            Eq. 1 expanded row by row with equal subproblems merged: a permanent
+                       for sparse matrices of any n <= 64 (independent of Ryser and of the walk).
 
 Parity of every function is pinned in ``tests/test_oracle_pins.py``.
 """
@@ -62,12 +64,15 @@ def load(path: str):
     L.oracle_nw2_range_u128.argtypes = [i32, p, u64, u64, pu64, pu64]
     L.oracle_band_dp_ld.argtypes = [i32, i32, p, pld]
     L.oracle_band_dp_u128.argtypes = [i32, i32, p, pu64, pu64]
+    L.oracle_rowdp_ld.argtypes = [i32, p, p, u64, pld]
+    L.oracle_rowdp_u128.argtypes = [i32, p, p, u64, pu64, pu64]
     L.oracle_nw_range_ld_mt.argtypes = [i32, p, u64, u64, i32, pld, pld]
     L.oracle_nw2_range_u128_mt.argtypes = [i32, p, u64, u64, i32, pu64, pu64]
     L.oracle_ld_to_dd.argtypes = [pld, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     for name in ("oracle_brute_ld", "oracle_brute_u128", "oracle_ryser_u128",
                  "oracle_ryser_gray_range_u128", "oracle_nw_range_ld", "oracle_nw_perm_ld",
                  "oracle_nw2_range_u128", "oracle_band_dp_ld", "oracle_band_dp_u128",
+                 "oracle_rowdp_ld", "oracle_rowdp_u128",
                  "oracle_nw_range_ld_mt", "oracle_nw2_range_u128_mt",
                  "oracle_long_double_bits", "oracle_long_double_mant_dig"):
         getattr(L, name).restype = ctypes.c_int
@@ -235,6 +240,46 @@ def band_dp(a, w: int) -> LD:
 def band_dp_int(a, w: int) -> int:
     a = _i64(a)
     v = _u128(lib().oracle_band_dp_u128, a.shape[0], w, _ptr(a))
+    return to_signed128(v & ((1 << 64) - 1), v >> 64)
+
+
+def rowdp_order(a) -> list[int]:
+    """A row order that keeps rowdp's states few: each next row is the one
+    whose nonzero columns add the fewest columns not yet touched (any order
+    gives the same permanent; this one only keeps the state sets small)."""
+    nz = np.asarray(a) != 0
+    n = nz.shape[0]
+    seen = np.zeros(n, dtype=bool)
+    left = list(range(n))
+    order = []
+    while left:
+        r = min(left, key=lambda i: (int((nz[i] & ~seen).sum()), i))
+        left.remove(r)
+        order.append(r)
+        seen |= nz[r]
+    return order
+
+
+def _order_arg(order, n):
+    o = np.ascontiguousarray(order if order is not None else range(n), dtype=np.int32)
+    assert o.shape == (n,)
+    return o
+
+
+def rowdp(a, order=None, max_states: int = 1 << 22) -> LD:
+    """perm(A) by rowdp in long double, rows in ``order`` (default: rowdp_order)."""
+    a = _f64(a)
+    o = _order_arg(rowdp_order(a) if order is None else order, a.shape[0])
+    out = ctypes.c_longdouble()
+    _check(lib().oracle_rowdp_ld(a.shape[0], _ptr(a), _ptr(o), max_states, ctypes.byref(out)), "rowdp")
+    return LD(out)
+
+
+def rowdp_int(a, order=None, max_states: int = 1 << 22) -> int:
+    """perm(A) by rowdp in integers modulo 2^128, signed."""
+    a = _i64(a)
+    o = _order_arg(rowdp_order(a) if order is None else order, a.shape[0])
+    v = _u128(lib().oracle_rowdp_u128, a.shape[0], _ptr(a), _ptr(o), max_states)
     return to_signed128(v & ((1 << 64) - 1), v >> 64)
 
 

@@ -23,6 +23,9 @@
  *   oracle_band_dp_ld / oracle_band_dp_u128  an independent permanent for banded
  *                                            matrices (row-by-row DP over the set of
  *                                            used columns in the band window)
+ *   oracle_rowdp_ld / oracle_rowdp_u128      an independent permanent for sparse
+ *                                            matrices: Eq. 1 expanded row by row,
+ *                                            equal subproblems merged
  *   oracle_*_mt                              the range functions above run on T
  *                                            POSIX threads over fixed, aligned chunks
  *                                            that are combined in chunk order, so the
@@ -373,6 +376,132 @@ int oracle_band_dp_u128(int n, int w, const int64_t *a, uint64_t *lo, uint64_t *
     u128_store(cur[NS - 1], lo, hi);
     free(cur); free(nxt); free(live); free(nlive);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 expanded row by row, with equal subproblems merged (a permanent for  */
+/* sparse matrices, independent of Ryser and of the Gray walk).  The rows are */
+/* taken in the order `order` (NULL: 0..n-1); a row order does not change a   */
+/* permanent.  After k rows a state is the set of columns those rows took;    */
+/* its weight is the sum, over the ways of reaching it, of the products of    */
+/* the entries taken.  Row order[k] extends every state by each of its        */
+/* nonzero columns that the state has not taken.  Two states that agree on    */
+/* the columns some later row can still take have the same futures, so a      */
+/* state keeps only those columns (reach[k+1]) and merged states add their    */
+/* weights.  After the last row the one state left is the empty set, and its  */
+/* weight is perm(A).  Returns -4 when more than max_states states are alive. */
+/* ------------------------------------------------------------------------ */
+
+#define ROWDP_EMPTY (~0ull)   /* never a state: a state has at most n-1 <= 63 columns */
+
+typedef struct {
+    uint64_t *key;
+    u128 *iv;           /* integer weights (rowdp_u128) */
+    ld *fv;             /* long double weights (rowdp_ld) */
+    size_t cap, count;
+} rowdp_map;
+
+static int rowdp_map_init(rowdp_map *m, size_t want, int is_int)
+{
+    size_t cap = 16;
+    while (cap < 2 * want) cap <<= 1;
+    m->cap = cap;
+    m->count = 0;
+    m->key = malloc(cap * sizeof(uint64_t));
+    m->iv = is_int ? calloc(cap, sizeof(u128)) : NULL;
+    m->fv = is_int ? NULL : calloc(cap, sizeof(ld));
+    if (!m->key || (is_int ? !m->iv : !m->fv)) return -3;
+    for (size_t h = 0; h < cap; ++h) m->key[h] = ROWDP_EMPTY;
+    return 0;
+}
+
+static void rowdp_map_free(rowdp_map *m)
+{
+    free(m->key);
+    free(m->iv);
+    free(m->fv);
+}
+
+/* the slot of state k (inserted with weight 0 if absent) */
+static size_t rowdp_slot(rowdp_map *m, uint64_t k)
+{
+    size_t h = (size_t)((k * 0x9E3779B97F4A7C15ull) >> 17) & (m->cap - 1);
+    while (m->key[h] != ROWDP_EMPTY && m->key[h] != k) h = (h + 1) & (m->cap - 1);
+    if (m->key[h] == ROWDP_EMPTY) {
+        m->key[h] = k;
+        m->count++;
+    }
+    return h;
+}
+
+static int rowdp(int n, const void *a, int is_int, const int *order, size_t max_states, u128 *iout, ld *fout)
+{
+    if (n < 1 || n > 64) return -1;
+    int row[64], seen[64] = {0};
+    for (int k = 0; k < n; ++k) {
+        row[k] = order ? order[k] : k;
+        if (row[k] < 0 || row[k] >= n || seen[row[k]]++) return -2;
+    }
+    const int64_t *ai = (const int64_t *)a;
+    const double *af = (const double *)a;
+    #define ROWDP_NZ(r, j) (is_int ? ai[(r) * n + (j)] != 0 : af[(r) * n + (j)] != 0.0)
+    uint64_t reach[65];   /* reach[k]: columns with a nonzero in rows row[k..n-1] */
+    reach[n] = 0;
+    for (int k = n - 1; k >= 0; --k) {
+        reach[k] = reach[k + 1];
+        for (int j = 0; j < n; ++j)
+            if (ROWDP_NZ(row[k], j)) reach[k] |= 1ull << j;
+    }
+    rowdp_map cur, nxt;
+    if (rowdp_map_init(&cur, 1, is_int)) { rowdp_map_free(&cur); return -3; }
+    size_t h0 = rowdp_slot(&cur, 0);
+    if (is_int) cur.iv[h0] = 1; else cur.fv[h0] = 1;
+    for (int k = 0; k < n; ++k) {
+        const int r = row[k];
+        int deg = 0;
+        for (int j = 0; j < n; ++j) deg += ROWDP_NZ(r, j);
+        size_t want = cur.count * (size_t)deg;
+        if (want > max_states) want = max_states;
+        if (rowdp_map_init(&nxt, want, is_int)) { rowdp_map_free(&cur); rowdp_map_free(&nxt); return -3; }
+        for (size_t h = 0; h < cur.cap; ++h) {
+            if (cur.key[h] == ROWDP_EMPTY) continue;
+            const uint64_t taken = cur.key[h];
+            for (int j = 0; j < n; ++j) {
+                if (!ROWDP_NZ(r, j) || ((taken >> j) & 1ull)) continue;
+                const uint64_t t = (taken | (1ull << j)) & reach[k + 1];
+                size_t g = rowdp_slot(&nxt, t);
+                if (nxt.count > max_states) { rowdp_map_free(&cur); rowdp_map_free(&nxt); return -4; }
+                if (is_int) nxt.iv[g] += cur.iv[h] * u128_from_i64(ai[r * n + j]);
+                else nxt.fv[g] += cur.fv[h] * (ld)af[r * n + j];
+            }
+        }
+        rowdp_map_free(&cur);
+        cur = nxt;
+    }
+    #undef ROWDP_NZ
+    u128 iv = 0;
+    ld fv = 0;
+    for (size_t h = 0; h < cur.cap; ++h)
+        if (cur.key[h] == 0) {   /* the empty set: every column taken and none reachable */
+            if (is_int) iv = cur.iv[h]; else fv = cur.fv[h];
+        }
+    rowdp_map_free(&cur);
+    if (iout) *iout = iv;
+    if (fout) *fout = fv;
+    return 0;
+}
+
+int oracle_rowdp_ld(int n, const double *a, const int *order, uint64_t max_states, long double *out)
+{
+    return rowdp(n, a, 0, order, (size_t)max_states, NULL, out);
+}
+
+int oracle_rowdp_u128(int n, const int64_t *a, const int *order, uint64_t max_states, uint64_t *lo, uint64_t *hi)
+{
+    u128 v = 0;
+    int rc = rowdp(n, a, 1, order, (size_t)max_states, &v, NULL);
+    if (rc == 0) u128_store(v, lo, hi);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

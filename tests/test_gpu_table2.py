@@ -83,3 +83,19 @@ def test_skip_fraction_is_bounded_by_the_all_zero_blocks(name):
     assert 0.0 <= r.zero_skip_frac <= z + 1e-12, (r.zero_skip_frac, z)
     if name != "mycielskian6":
         assert r.zero_skip_frac > 0.5 * z, (r.zero_skip_frac, z)
+
+
+def test_whole_walk_of_the_bcspwr02_shape_against_the_row_dp():
+    """The whole 2^48-step walk of the bcspwr02 shape (n = 49, all ones; about
+    a second, because the zero spans remove nearly all of it): exact, bit for
+    bit against the oracle's row-expansion DP (Eq. 1); the same matrix with
+    its columns permuted (perm(AQ) = perm(A)); and the FP64 walk."""
+    a = synth.table2_like("bcspwr02")
+    want = oracle.rowdp_int(a)
+    r = A.permanent(a)
+    assert r.value == want
+    assert r.zero_skip_frac > 0.99
+    q = np.random.default_rng(49).permutation(a.shape[0])
+    assert A.permanent(np.ascontiguousarray(a[:, q])).value == want
+    rf = A.permanent(a.astype(np.float64), flags=A.PERM_FLAG_ABS_SUM)
+    assert abs(rf.value - want) <= max(1e-9 * want, 64 * 49 * U * rf.abs_term_sum)

@@ -32,6 +32,10 @@ MUTATIONS = {
     "nw2_shift_sign": ("x2[i] = 2 * u128_from_i64(a[i * n + (n - 1)]) - rowsum;", "x2[i] = 2 * u128_from_i64(a[i * n + (n - 1)]) + rowsum;"),
     "band_no_preset_past_end": ("                if (!col_exists(n, i + 1 + w)) u |= 1 << (W - 1);\n                nxt[u] += cur[s] * v;", "                nxt[u] += cur[s] * v;"),
     "band_wrong_window": ("                int c = i - w + k;\n                if (!col_exists(n, c)) continue;\n                ld v", "                int c = i - w + k + 1;\n                if (!col_exists(n, c)) continue;\n                ld v"),
+    "rowdp_reuses_columns": ("if (!ROWDP_NZ(r, j) || ((taken >> j) & 1ull)) continue;", "if (!ROWDP_NZ(r, j)) continue;"),
+    "rowdp_forgets_taken": ("const uint64_t t = (taken | (1ull << j)) & reach[k + 1];", "const uint64_t t = (1ull << j) & reach[k + 1];"),
+    "rowdp_weight_transposed": ("if (is_int) nxt.iv[g] += cur.iv[h] * u128_from_i64(ai[r * n + j]);", "if (is_int) nxt.iv[g] += cur.iv[h] * u128_from_i64(ai[j * n + r]);"),
+    "rowdp_ld_drops_weight": ("else nxt.fv[g] += cur.fv[h] * (ld)af[r * n + j];", "else nxt.fv[g] += cur.fv[h];"),
     "mt_chunk_short": ("uint64_t lo = jb->g_lo + c * jb->chunk, hi = lo + jb->chunk;", "uint64_t lo = jb->g_lo + c * jb->chunk, hi = lo + jb->chunk - (c == 3);"),
 }
 
@@ -52,6 +56,8 @@ PIN_TESTS = [
     lambda: [pins.test_band_dp_matches_brute_force(n, w) for n in (3, 5, 8) for w in (1, 2, 3)],
     pins.test_band_dp_fibonacci_and_rejects_offband,
     pins.test_band_dp_matches_nw_on_band_sibling,
+    lambda: [pins.test_rowdp_matches_brute_force_in_any_row_order(n) for n in (3, 5, 8)],
+    pins.test_rowdp_closed_forms,
 ]
 
 

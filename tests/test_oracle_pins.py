@@ -277,6 +277,55 @@ def test_band_dp_matches_nw_on_band_sibling():
     assert abs(float(oracle.band_dp(a, 3)) - float(got)) <= 1e-15 * float(absum)
 
 
+# --------------------------------------------------------------------------- row-expansion DP
+
+def sparse_int(n, density, seed, lo=-3, hi=4):
+    g = np.random.default_rng(seed)
+    pat = g.random((n, n)) < density
+    np.fill_diagonal(pat, True)
+    return (g.integers(lo, hi, size=(n, n)) * pat).astype(np.int64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8])
+def test_rowdp_matches_brute_force_in_any_row_order(n):
+    """Eq. 1 by brute force, for every row order tried (signed integers and
+    signed reals, with zeros)."""
+    g = np.random.default_rng(n)
+    a = sparse_int(n, 0.5, 70 + n)
+    af = rand_real(n, 80 + n, density=0.6, signed=True)
+    for _ in range(3):
+        order = list(g.permutation(n))
+        assert oracle.rowdp_int(a, order) == oracle.brute_int(a)
+        assert rel(oracle.rowdp(af, order), oracle.brute(af)) < 1e-15 or abs(float(oracle.brute(af))) < 1e-300
+    assert oracle.rowdp_int(a) == oracle.brute_int(a)
+
+
+def test_rowdp_matches_ryser_and_band_dp():
+    a = sparse_int(20, 0.15, 5)
+    assert oracle.rowdp_int(a) == oracle.ryser_gray(a)
+    b = synth.band_plus(n=40, w=3, extra=0, seed=2, values="01")
+    assert oracle.rowdp_int(b) == oracle.band_dp_int(b, 3)
+    assert oracle.rowdp_int(b, list(range(39, -1, -1))) == oracle.band_dp_int(b, 3)
+
+
+def test_rowdp_closed_forms():
+    """n! for the all-ones matrix, derangements for J - I, 1 for a permutation
+    matrix, Fibonacci numbers for tridiagonal ones (n = 64: every column bit)."""
+    for n in (6, 12):
+        assert oracle.rowdp_int(synth.ones(n)) == math.factorial(n)
+        assert oracle.rowdp_int(synth.ones_minus_identity(n)) == derangements(n)
+    assert oracle.rowdp_int(synth.permutation_matrix(50, 3)) == 1
+    assert oracle.rowdp_int(synth.tridiagonal_ones(64)) == fibonacci(65)
+    assert rel(oracle.rowdp(synth.tridiagonal_ones(64).astype(float)), fibonacci(65)) < 1e-15
+
+
+def test_rowdp_limits_and_bad_orders():
+    with pytest.raises(ValueError):
+        oracle.rowdp_int(synth.ones(14), max_states=100)
+    with pytest.raises(ValueError):
+        oracle.rowdp_int(synth.ones(4), [0, 1, 1, 3])
+
+
 # --------------------------------------------------------------------------- cross-formula
 
 def test_all_formulas_agree_on_integer_er():
