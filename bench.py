@@ -224,8 +224,8 @@ def run_reference(args):
 def extras(A, sh, a, first):
     """What the single-matrix line carries beside its headline (one GPU only):
     the batch and serving workloads, accuracy against the oracle on every
-    workload, the first (cold) call on a matrix never seen before, and the
-    FP64 CPU baseline."""
+    workload, the first (cold) call on a matrix never seen before, the FP64
+    CPU baseline, and the Table II-shaped suite."""
     from paper_2501_15126_gb300 import synth
     out = {}
     out["batch"] = measure_batch(A, sh)
@@ -262,6 +262,7 @@ def extras(A, sh, a, first):
         "cfg3_n48": "whole 2^47-step exact walks: bench.py --workload cfg3 (profiles/cfg3_n48_full_permanent.md)"}
     out["exact_roofline"] = exact_roofline(A, sh)
     out["cpu_fp64_baseline"] = cpu_fp64_baseline(a)
+    out["table2"] = measure_table2(A)
     return out
 
 
@@ -704,17 +705,16 @@ def zero_product_fraction(a, samples=1 << 16, seed=11):
     return float(((x0[None, :] + S @ a[:, : n - 1].T) == 0).any(axis=1).mean())
 
 
-def run_table2(args, seconds_per_range=0.25):
+def measure_table2(A, seconds_per_range=0.25, cpu_seconds=1.0):
     """Matrices with the shapes of the paper's real-life set (Table II; values
     as Sec. VI-E describes them): the library's default plan timed by CUDA
     events on four Gray sub-ranges spread over the walk (their sizes picked
     for about `seconds_per_range` each), the fraction of blocks the zero skip
     removed, the fraction of zero products (host sample), the projected time
-    of the whole walk, and CPU-SparsePerman (FP64, zero tracking) on a prefix."""
-    import torch
-    from paper_2501_15126_gb300 import _abi as A
+    of the whole walk, and CPU-SparsePerman (FP64, zero tracking) on a prefix.
+    The bcspwr02 shape's whole walk (n = 49) is computed and compared with the
+    oracle's row-expansion DP."""
     from paper_2501_15126_gb300 import synth
-    torch.cuda.set_device(0)
     out = {"workload": "table2", "note": "random matrices with Table II's n, nnz, symmetry and value structure "
                                          "(not the SuiteSparse matrices)", "matrices": {}}
     for sh in synth.TABLE2_SHAPES:
@@ -738,7 +738,7 @@ def run_table2(args, seconds_per_range=0.25):
             steps += r.steps
             skipped += r.zero_skip_frac * r.steps
         rate = steps / (ms / 1e3)
-        cpu = cpu_fp64_baseline(a.astype(np.float64), seconds_hint=2.0)
+        cpu = cpu_fp64_baseline(a.astype(np.float64), seconds_hint=cpu_seconds)
         rec = {"n": n, "nnz": int(np.count_nonzero(a)), "values": sh.values,
                "arithmetic": "exact (%d-bit ring)" % (64 * first.exact_words) if first.vtype == A.PERM_I64 else "fp64",
                "engine": "codegen" if first.engine == A.PERM_ENGINE_CODEGEN else "generic",
@@ -751,7 +751,26 @@ def run_table2(args, seconds_per_range=0.25):
                "cpu_sparseperman_fp64_steps_per_s": cpu["value"], "cpu_cores": cpu["cores"],
                "gpu_over_cpu": rate / cpu["value"]}
         out["matrices"][sh.name] = rec
-        print(json.dumps({sh.name: rec}), flush=True)
+    import oracle
+    a = synth.table2_like("bcspwr02")
+    t0 = time.perf_counter()
+    r = A.permanent(a)
+    wall = time.perf_counter() - t0
+    want = oracle.rowdp_int(a)
+    out["bcspwr02_whole_walk"] = {"n": 49, "gray_steps": 1 << 48, "value": str(r.value), "oracle_rowdp": str(want),
+                                  "matches": r.value == want, "ms_kernel": r.ms_kernel, "seconds_end_to_end": wall,
+                                  "zero_skip_frac": r.zero_skip_frac,
+                                  "note": "exact walk of all 2^48 Gray steps; oracle: Eq. 1 expanded row by row"}
+    return out
+
+
+def run_table2(args):
+    import torch
+    from paper_2501_15126_gb300 import _abi as A
+    torch.cuda.set_device(0)
+    out = measure_table2(A, cpu_seconds=2.0)
+    for name, rec in out["matrices"].items():
+        print(json.dumps({name: rec}), flush=True)
     print(json.dumps(out))
     return 0
 

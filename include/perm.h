@@ -195,7 +195,12 @@ typedef struct {
     double fp_ops_per_step;/* counted arithmetic ops per Gray step (cost model): FP64 */
                            /*   operations, or on the exact path integer multiply     */
                            /*   operations (perm_inspect_t.ring_ops_per_step)         */
-    double zero_skip_frac; /* fraction of 2^B-step blocks skipped as all-zero         */
+    double zero_skip_frac; /* fraction of the walk skipped as all-zero: of the warp's */
+                           /*   2^B-step blocks (32 chunks each, idle lanes of a      */
+                           /*   range's last task included) for the block walks, of   */
+                           /*   the threads' steps for PERM_ENGINE_XSHARED; 0 for the */
+                           /*   direct kernel (n <= 8).  Sec. VI-E: repeated values   */
+                           /*   leave zero entries in x; zero spans skip them.        */
     /* FP64 inputs: sum over the walk's Gray indices of |prod_i x_i(g)|, times 2 for
        a whole walk (the scale of the permanent), raw for a sub-range.  It is
        accumulated in FP32 on the GPU (relative accuracy about 1e-5); terms below

@@ -568,6 +568,18 @@ void describe(const perm_plan_s &P, perm_result_t *out) {
 
 // Turns a reduced raw sum (2 words FP64 hi/lo, or w exact words) into the
 // permanent (or the sub-range partial sum).
+// The skip counter's meaning per engine: the shared-memory walk counts the
+// steps each thread skipped; the block walks count warp blocks (a skip is
+// warp-wide, and lane 0 counts it once), out of ntasks 2^(K-B) warp blocks
+// (a range's idle lanes of its last task walk in step with the warp).
+double zero_skip_fraction(const perm_plan_s &P, uint64_t skipped) {
+    if (P.direct) return 0.0;
+    if (P.engine == PERM_ENGINE_XSHARED) return P.g_hi > P.g_lo ? (double)skipped / (double)(P.g_hi - P.g_lo) : 0.0;
+    const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
+    const uint64_t warp_blocks = P.ntasks << std::max(0, P.K - B);
+    return warp_blocks ? (double)skipped / (double)warp_blocks : 0.0;
+}
+
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *r, perm_result_t *out) {
     const int n = P.m.n;
     if (P.zero) { out->status = PERM_OK; return PERM_OK; }
@@ -629,14 +641,7 @@ perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out) {
         out->status = PERM_ERR_TIMEOUT;
         return fail(PERM_ERR_TIMEOUT, "device-side deadline passed; the walk stopped early");
     }
-    const uint64_t skipped = P.h_res[1];
-    if (P.engine == PERM_ENGINE_XSHARED) {   // counts skipped steps, not blocks
-        out->zero_skip_frac = (double)skipped / (double)(P.g_hi - P.g_lo);
-    } else {
-        const int B = P.engine == PERM_ENGINE_GENERIC ? P.gf.block_log2 : P.cg.block_log2;
-        const uint64_t blocks = (P.g_hi - P.g_lo) >> std::max(1, B);
-        out->zero_skip_frac = (!P.direct && blocks) ? (double)skipped / (double)blocks : 0.0;
-    }
+    out->zero_skip_frac = zero_skip_fraction(P, P.h_res[1]);
     return finish_raw(P, P.h_res + 2, out);
 }
 

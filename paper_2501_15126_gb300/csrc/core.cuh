@@ -77,13 +77,6 @@ __device__ __forceinline__ u64 warp_or64(u64 v) {
     return ((u64)hi << 32) | lo;
 }
 
-// Sum of a 64-bit value over the 32 lanes of a (converged) warp, in every lane.
-__device__ __forceinline__ u64 warp_sum64(u64 v) {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(PERM_FULLMASK, v, d);
-    return v;
-}
-
 // Nanoseconds from the GPU's global timer (0 when the walk code runs as
 // host C++ in the emulation tests).
 __device__ __forceinline__ u64 global_ns() {
@@ -735,18 +728,13 @@ __device__ __forceinline__ void walk_tasks(Pol &pol, const WalkArgs &wa) {
         u64 q = wa.chunk_lo + task * 32ull + (u64)lane;
         const bool live = q < wa.chunk_hi;
         if (!live) q = wa.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
-        const u64 skipped_before = skipped;
         typename A::Acc acc = walk_chunk<Pol, A, Bv>(pol, q, wa.K, wa.zero_skip, skipped);
-        if (!live) {
-            acc = A::acc_zero();
-            skipped = skipped_before;
-        }
+        if (!live) acc = A::acc_zero();
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
         if (lane == 0) A::acc_store(wa.task_out + task * (u64)A::ACC_WORDS, acc);
     }
-    // every lane counts its own skipped blocks (of live chunks)
-    skipped = warp_sum64(skipped);
+    // the warp's skipped blocks (a skip is warp-wide: one count per warp block)
     if (wa.skip_counter && lane == 0 && skipped) atomicAdd(wa.skip_counter, skipped);
 }
 

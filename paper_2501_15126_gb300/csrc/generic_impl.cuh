@@ -403,12 +403,11 @@ __device__ __forceinline__ typename A::Acc walk_chunk_compact(GenericPol<NMAX, A
         // data-driven loops of the flips
         const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(qB));
         if (zero_skip && all_zero) {
-            // the widest all-zero span that starts here (core.cuh: zero_span)
-            // and its net effect on x
-            const int m = zero_span<GenericPol<NMAX, A>, Bv>(pol, h, K);
-            pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
-            skipped += 1ull << m;
-            h += (1ull << m) - 1;
+            // the block's net effect on x.  (This walk does not widen the skip
+            // into zero spans: on the small exact matrices it serves, the
+            // wider skip path cost more than the spans saved.)
+            pol.flip_dyn(Bv - 1, x, s_mid);
+            ++skipped;
             continue;
         }
         typename A::Blk blk = A::blk_zero();
@@ -471,22 +470,17 @@ __device__ __forceinline__ void generic_task_loop(const BatchArgs &ba, unsigned 
         const bool live = q < bm.chunk_hi;
         if (!live) q = bm.chunk_hi - 1;     // idle lanes shadow a real chunk to stay in step
         GenericPol<NMAX, A> pol(slot, bm.abs_shift);
-        const u64 skipped_before = skipped;
         typename A::Acc acc;
         if constexpr (GenericPol<NMAX, A>::kDual)
             acc = walk_chunk_dual<GenericPol<NMAX, A>, A, PERM_GENERIC_B>(pol, q, bm.K, ba.zero_skip, skipped);
         else
             acc = walk_chunk_compact<NMAX, A>(pol, q, bm.K, ba.zero_skip, skipped);
-        if (!live) {
-            acc = A::acc_zero();
-            skipped = skipped_before;
-        }
+        if (!live) acc = A::acc_zero();
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) acc = A::acc_add(acc, A::shfl_down(acc, d));
         if (lane == 0) A::acc_store(ba.task_out + (bm.out_offset + (task - bm.task_begin)) * (u64)A::ACC_WORDS, acc);
     }
-    // every lane counts its own skipped blocks (of live chunks)
-    skipped = warp_sum64(skipped);
+    // the warp's skipped blocks (a skip is warp-wide: one count per warp block)
     if (ba.skip_counter && lane == 0 && skipped) atomicAdd(ba.skip_counter, skipped);
 }
 

@@ -170,8 +170,7 @@ perm_status_t walk_in_scratch(perm_plan_s &P, unsigned char *scratch, cudaStream
     if ((e = cudaStreamSynchronize(st_)) != cudaSuccess) return failed(cuda_fail(e, "cudaStreamSynchronize"));
     describe(P, out);
     if (host[3]) return failed(fail(PERM_ERR_TIMEOUT, "device-side deadline passed; the walk stopped early"));
-    const uint64_t blocks = (P.g_hi - P.g_lo) >> P.gf.block_log2;
-    out->zero_skip_frac = (!P.direct && blocks) ? (double)host[1] / (double)blocks : 0.0;
+    out->zero_skip_frac = zero_skip_fraction(P, host[1]);
     return finish_raw(P, raw, out);
 }
 

@@ -113,6 +113,8 @@ perm_status_t plan_launch(perm_plan_s &P, cudaStream_t st, bool record_events = 
 perm_status_t plan_finish(perm_plan_s &P, perm_result_t *out);
 void describe(const perm_plan_s &P, perm_result_t *out);
 perm_status_t finish_raw(const perm_plan_s &P, const uint64_t *raw, perm_result_t *out);
+// perm_result_t.zero_skip_frac from the walk's skip counter
+double zero_skip_fraction(const perm_plan_s &P, uint64_t skipped);
 int nmax_bucket(int n);
 // Matrix images; img is kImgF64, kImgInt or kImgDD.
 void build_devmat(const Matrix &m, const Layout &L, int img, int nmax, std::vector<unsigned char> &img_out);

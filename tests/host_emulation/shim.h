@@ -27,7 +27,6 @@ static perm_dim3 threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0}, blockDim = {32, 1,
 
 template <class T> inline T __shfl_sync(unsigned, T v, int) { return v; }
 template <class T> inline T __shfl_down_sync(unsigned, T v, int) { return v; }
-template <class T> inline T __shfl_xor_sync(unsigned, T v, int) { return T(0); }   // the other lanes hold 0
 inline unsigned __reduce_or_sync(unsigned, unsigned v) { return v; }
 inline bool __all_sync(unsigned, bool p) { return p; }
 inline void __syncwarp() {}
