@@ -786,6 +786,9 @@ def run_profile_case(args):
     if args.profile_matrix == "batch28":
         # the largest class of the batch workload: its first n=28 matrix with these values
         a = next(it.a for it in synth.batch(count=400) if it.a.shape[0] == 28 and it.values == vals)
+    elif args.profile_matrix in [t.name for t in synth.TABLE2_SHAPES]:
+        a = synth.table2_like(args.profile_matrix)
+        vals = "01" if a.dtype == np.int64 else "f64"
     elif args.profile_exact or args.profile_matrix == "band48":
         a = synth.band_plus(48, 3, 2, seed=3, values=vals)
     else:
@@ -828,9 +831,12 @@ def main():
     ap.add_argument("--profile-exact", action="store_true")
     ap.add_argument("--profile-chunk-log2", type=int, default=0, help="profile: K (0 = the plan's choice)")
     ap.add_argument("--profile-engine", default="codegen", choices=["codegen", "generic"])
-    ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28", "band48"],
+    ap.add_argument("--profile-matrix", default="bench", choices=["bench", "batch28", "band48", "bcsstk01",
+                                                                  "mycielskian6", "mesh1e1", "bcspwr02", "curtis54",
+                                                                  "d_ss"],
                     help="bench: the n=36 bench matrix (the n=48 band with --profile-exact); "
-                         "batch28: an n=28 matrix of the batch workload; band48: the n=48 band-plus-off-band matrix")
+                         "batch28: an n=28 matrix of the batch workload; band48: the n=48 band-plus-off-band matrix; "
+                         "the Table II shape names: that suite's matrix")
     ap.add_argument("--profile-paired", action="store_true",
                     help="generated FP64 kernels: the paired chain even where two-state chains are cheaper")
     ap.add_argument("--batch-count", type=int, default=10_000)

@@ -142,7 +142,11 @@ typedef struct {
     int32_t reg_rows;      /* codegen: rows of x kept in registers (k of Algorithm 4);     */
                            /*   0 = Algorithm 4 decides, n = all in registers              */
     int32_t chunk_log2;    /* K: each thread walks aligned chunks of 2^K Gray indices;     */
-                           /*   0 = auto                                                   */
+                           /*   0 = auto; a K below the kernel's unrolled block (2^5      */
+                           /*   steps; 2^7 for generated FP64 kernels unless most terms   */
+                           /*   of the walk are zero) is raised to it,                    */
+                           /*   and a range must be aligned to the chunk (else           */
+                           /*   PERM_ERR_ARG)                                              */
     int32_t threads;       /* resident threads of the persistent grid; 0 = auto            */
     int32_t exact_words;   /* exact path modulus 2^(64w): 0 = smallest w the bound allows, */
                            /*   and a whole walk then runs in the narrowest ring of 32-bit */

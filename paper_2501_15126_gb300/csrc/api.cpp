@@ -306,6 +306,8 @@ perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, i
         const double want_tasks = 64.0 * (double)resident_warps;   // keeps the last round of tasks short
         K = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * want_tasks)));
         K = std::max(K, block_log2 + 3);
+    } else {
+        K = std::max(K, block_log2);   // a chunk holds whole blocks
     }
     K = std::min(K, kmax);
     if (K < block_log2) return fail(PERM_ERR_ARG, "range too short or misaligned for the chunk size");
@@ -333,9 +335,8 @@ void split_for_rows(const Layout &L, int rows, int *k, int *c) {
 
 // The generated kernel keeps every row reached inside the unrolled block in
 // registers: c >= B.  k = n means no global rows.
-void normalise_split(const Layout &L, int *k, int *c) {
+void normalise_split(const Layout &L, int B, int *k, int *c) {
     const int n = L.n;
-    const int B = CodegenKernel().block_log2;
     if (*c < B) { *c = std::min(B, n - 1); *k = L.group_begin[*c]; }
     if (*c >= n - 1 || *k >= n) { *k = n; *c = n - 1; }
     if (*k < 1) *k = 1;
@@ -348,9 +349,12 @@ static void codegen_layout(perm_plan_s &P) {
     const int n = P.m.n;
     int k = n, c = n - 1;
     const double gr = P.opts.gr_ratio > 0 ? P.opts.gr_ratio : kDefaultGRRatio;
+    // FP64 walks where most terms are zero (repeated values, Sec. VI-E) keep
+    // short blocks, so that the zero skip starts at 2^5 steps
+    P.zero_heavy = P.arith == 0 && zero_term_fraction(P.m, P.L.col_order, 1024) > 0.25;
     partition_alg4(P.L, gr, kCodegenBaseRegs, &k, &c);   // Algorithm 4
     if (P.opts.reg_rows > 0) split_for_rows(P.L, P.opts.reg_rows, &k, &c);
-    normalise_split(P.L, &k, &c);
+    normalise_split(P.L, codegen_block_log2(P), &k, &c);
     P.pure_reg = (P.opts.flags & PERM_FLAG_PURE_REG) != 0;
     // the middle tier: shared memory holds up to 96 KB of x per 256-thread block
     // (two blocks per SM), i.e. 48 FP64 or 96 int32 rows

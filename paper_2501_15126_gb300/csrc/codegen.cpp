@@ -41,7 +41,15 @@ namespace perm {
 
 namespace {
 
-constexpr int kCodegenBlockLog2 = 5;
+// Steps per unrolled block, log2.  FP64 walks take longer blocks: the block
+// start (run-time flip, chain rebuild, vote) is then spread over more steps
+// (the n=36 FP64 walk: 370.9 ms at 2^5, 365.5 at 2^6, 361.5 at 2^7), and
+// their compile time grows little (0.64 -> 0.76 s).  Exact walks keep 2^5: at
+// 2^6 their NVRTC time grows by half and some need all 255 registers.  So
+// do FP64 walks where most terms are zero: their zero skip starts at a block
+// (the d_ss shape: 1.66e12 Gray steps/s at 2^5, 0.98e12 at 2^7).
+constexpr int kCodegenBlockLog2F64 = 7;
+constexpr int kCodegenBlockLog2Exact = 5;
 constexpr int kCodegenBlock = 256;
 
 // ------------------------------------------------------------------ driver API via the runtime
@@ -271,7 +279,7 @@ struct Emitter {
     }
 
     std::string emit() {
-        const int B = kCodegenBlockLog2;
+        const int B = codegen_block_log2(P);
         const std::vector<int> hi = high_levels(B);
         o << "// generated: permanent walk for one " << n << "x" << n << " matrix\n";
         o << "// order=" << P.L.ordering << " reg_rows(k)=" << k << " reg_cols(c)=" << c << " B=" << B << "\n";
@@ -532,6 +540,10 @@ constexpr size_t kCacheMax = 512;
 
 bool codegen_no_fold() { return no_fold_env(); }
 
+int codegen_block_log2(const perm_plan_s &P) {
+    return P.arith == 0 && !P.zero_heavy ? kCodegenBlockLog2F64 : kCodegenBlockLog2Exact;
+}
+
 std::string codegen_source(const perm_plan_s &P) {
     Emitter e(P, codegen_min_blocks(P));
     return e.emit();
@@ -592,7 +604,7 @@ perm_status_t same_on_probe(const perm_plan_s &P, const CacheEntry &a, const Cac
                             std::string &err) {
     Driver &d = driver();
     const int n = P.m.n;
-    const int K = std::min(n - 1, kCodegenBlockLog2 + 3);
+    const int K = std::min(n - 1, codegen_block_log2(P) + 3);
     const uint64_t chunks = std::min<uint64_t>(P.total >> K, 64 * 32);
     const uint64_t ntasks = (chunks + 31) / 32;
     const int words = P.arith;
@@ -649,7 +661,7 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     if (!d.ok) { err = "CUDA driver entry points unavailable"; return PERM_ERR_CUDA; }
     const std::string src = codegen_source(P);
     P.cg.block = kCodegenBlock;
-    P.cg.block_log2 = kCodegenBlockLog2;
+    P.cg.block_log2 = codegen_block_log2(P);
     const bool use_cache = !(P.opts.flags & PERM_FLAG_NO_KERNEL_CACHE);
     if (use_cache) {
         std::lock_guard<std::mutex> lk(g_cache_mu);

@@ -28,6 +28,9 @@ struct CodegenKernel {
     bool owned = false;         // not in the cache: unloaded with the plan
 };
 
+// log2 of the generated kernel's unrolled block for the plan's arithmetic.
+int codegen_block_log2(const perm_plan_s &P);
+
 // The CUDA C++ text for the plan's matrix, order and split (P.k, P.c).
 std::string codegen_source(const perm_plan_s &P);
 

@@ -529,4 +529,35 @@ std::vector<Launch> alg2_launches(int64_t tau, int n) {
     return out;
 }
 
+double zero_term_fraction(const Matrix &m, const int *col_order, int samples) {
+    const int n = m.n;
+    if (n < 2 || samples < 1) return 0.0;
+    double x0[kNMax];
+    for (int i = 0; i < n; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < n; ++j) rs += m.fval(i, j);
+        x0[i] = m.fval(i, col_order[n - 1]) - 0.5 * rs;
+    }
+    uint64_t state = 0x9e3779b97f4a7c15ull;   // splitmix64
+    auto next = [&state]() {
+        uint64_t z = (state += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    };
+    int zero = 0;
+    for (int t = 0; t < samples; ++t) {
+        const uint64_t S = next();
+        bool any = false;
+        for (int i = 0; i < n && !any; ++i) {
+            double x = x0[i];
+            for (int p = 0; p < n - 1; ++p)
+                if (((S >> p) & 1ull) && m.nz(i, col_order[p])) x += m.fval(i, col_order[p]);
+            any = x == 0.0;
+        }
+        zero += any;
+    }
+    return (double)zero / samples;
+}
+
 }  // namespace perm

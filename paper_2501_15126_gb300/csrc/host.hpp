@@ -77,6 +77,12 @@ void order_alg3(const Matrix &m, int *col_order, int *row_order);
 // inside a group in the order the rows were first touched.
 Layout make_layout(const Matrix &m, const int *col_order, int ordering);
 
+// Fraction of the walk's terms (Algorithm 1: the subsets of the first n-1
+// ordered columns) whose product has a zero factor, estimated from `samples`
+// subsets drawn by a fixed-seed generator (each column in with probability
+// 1/2): x_i = a_{i,last} - (1/2) sum_j a_ij + the subset's entries of row i.
+double zero_term_fraction(const Matrix &m, const int *col_order, int samples);
+
 // Arithmetic ops per Gray step (Lemma 2 weights 2^(n-j-2)/(2^(n-1)-1)):
 // chain scheme: nnz_j updates + |R_0|+...+|R_j| multiplies + 1 accumulate;
 // paper scheme: nnz_j updates + (n-1) multiplies + 1 accumulate.

@@ -41,7 +41,7 @@ int main(int argc, char **argv) {
     unsigned long long q;
     while (std::scanf("%llu", &q) == 1) {
         unsigned long long skipped = 0, w[6] = {0, 0, 0, 0, 0, 0};
-        const auto acc = pk::walk_chunk<pk::GenPol, pk::A, 5>(pol, q, K, 1, skipped);
+        const auto acc = pk::walk_chunk<pk::GenPol, pk::A, PERM_TEST_B>(pol, q, K, 1, skipped);
         pk::A::acc_store(w, acc);
         std::printf("%llu", q);
         for (int i = 0; i < pk::A::ACC_WORDS; ++i) std::printf(" %016llx", w[i]);
@@ -59,8 +59,10 @@ def emulate(source, K, chunks, init):
         open(os.path.join(d, "walk.cu"), "w").write(source)
         open(os.path.join(d, "main.cpp"), "w").write(HARNESS)
         exe = os.path.join(d, "walk")
+        B = int(re.search(r" B=(\d+)", source).group(1))   # the kernel's unrolled block, log2
         subprocess.check_call(["g++", "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined",
                                "-fno-sanitize-recover=all", "-ftrivial-auto-var-init=" + init,
+                               "-DPERM_TEST_B=%d" % B,
                                "-I", os.path.join(HERE, "host_emulation"), "-I", CSRC, "-I", d,
                                os.path.join(d, "main.cpp"), "-o", exe])
         out = subprocess.run([exe, str(K)], input=" ".join(map(str, chunks)), capture_output=True, text=True,

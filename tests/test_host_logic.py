@@ -229,6 +229,27 @@ def test_generated_fp64_kernel_picks_the_cheaper_chain():
     assert "kDual = false" in A.codegen_source(synth.band_plus(48, 3, 2, seed=3, values="01"))   # exact: one chain
 
 
+def test_generated_block_length_follows_arithmetic_and_zeros():
+    """Generated kernels unroll 2^7-step blocks for FP64 walks and 2^5 for exact
+    ones, and for FP64 walks where most terms have a zero factor (repeated
+    values, Sec. VI-E), so that their zero skip starts at 2^5 steps.  The
+    FP64 kernel's split keeps every row reached inside a block in registers
+    (c >= B)."""
+    import re
+
+    def header(a, **kw):
+        m = re.search(r"reg_cols\(c\)=(\d+) B=(\d+)", A.codegen_source(a, **kw))
+        return int(m.group(1)), int(m.group(2))
+    for a, B in [(synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True), 7),
+                 (synth.table2_like("mesh1e1"), 7),
+                 (synth.table2_like("d_ss"), 5),
+                 (synth.table2_like("curtis54").astype(np.float64), 5),
+                 (synth.table2_like("curtis54"), 5),
+                 (synth.band_plus(48, 3, 2, seed=3, values="01"), 5)]:
+        c, b = header(a)
+        assert b == B and c >= B, (a.shape, a.dtype, b, c)
+
+
 def test_order_search_lowers_the_walk_cost_model():
     """The AUTO order search (FP64 walks of 2^30 steps and more) only accepts
     column swaps that lower the cost model of the scheme the walk runs; its
