@@ -297,6 +297,7 @@ struct Emitter {
         // paired step scales its column-0 products by 2^-SH0 and Q_1 by the rest
         o << "    static constexpr int abs_shift = " << (P.arith == 0 ? P.abs_shift : 0) << ";\n";
         o << "    static constexpr bool kAbs = " << (P.want_abs ? "true" : "false") << ";\n";
+        o << "    static constexpr bool kZeroSpans = " << (P.zero_spans ? "true" : "false") << ";\n";
         if (P.dual) {
             for (int g : high_levels2(B)) o << "    P QA" << g << ", QB" << g << ";\n";
         } else if (!P.pure_reg) {
@@ -305,7 +306,7 @@ struct Emitter {
         // level L >= B of the chain(s) is zero: the stored level at the first
         // nonempty group >= L (the zero spans of core.cuh)
         o << "    __device__ __forceinline__ bool level_zero(int L) const {\n";
-        if (!P.pure_reg) {
+        if (!P.pure_reg && P.zero_spans) {
             o << "        switch (L) {\n";
             for (int L = B; L < n; ++L) {
                 int g = -1;

@@ -514,6 +514,7 @@ struct PairSteps {
 // so the search climbs until a level is nonzero in some lane.
 template <class Pol, int Bv>
 __device__ __forceinline__ int zero_span(const Pol &pol, u64 h, int K) {
+    if constexpr (!Pol::kZeroSpans) return 0;   // a kernel built without the wider skip
     const int t = h ? ctz64(h) : K - Bv;
     int m = 0;
     while (m < t && __all_sync(PERM_FULLMASK, pol.level_zero(Bv + m + 1))) ++m;
@@ -607,27 +608,43 @@ __device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int 
     typename A::Acc acc = A::acc_zero();
     typename A::Blk mid = A::blk_zero();
     const u64 nblocks = 1ull << (K - Bv);
-    for (u64 h = 0; h < nblocks; ++h) {
+    u64 h = 0;
+    int fj = -1, fs = 1;   // the run-time flip due before block h (see walk_chunk_single)
+    bool net = false;
+    for (;;) {
+        if (fj >= 0) {
+            pol.flip_dyn(fj, x, fs);
+            if (net) {
+                net = false;
+                if (h >= nblocks) break;
+                fj = Bv + ctz64(h);
+                fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
+                continue;
+            }
+            pol.chain_hi2(fj, x, QA, QB);
+        }
         if (h != 0 && (h & 7) == 0) {
             A::acc_merge(acc, mid);
             mid = A::blk_zero();
         }
         const u64 gb = g0 + (h << Bv);
-        if (h != 0) {
-            const int j = Bv + ctz64(h);
-            const int s = ((gb >> (j + 1)) & 1ull) ? -1 : 1;
-            pol.flip_dyn(j, x, s);
-            pol.chain_hi2(j, x, QA, QB);
-        }
         const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
         // the vote is also the warp's reconvergence point (see walk_chunk_single)
         const bool all_zero = __all_sync(PERM_FULLMASK, A::is_zero(QA) && A::is_zero(QB));
         if (zero_skip && all_zero) {
             const int m = zero_span<Pol, Bv>(pol, h, K);
-            if (m == 0) pol.template flip_rt<Bv - 1>(x, s_mid);
-            else pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
             skipped += 1ull << m;
-            h += (1ull << m) - 1;
+            if (m == 0) {
+                pol.template flip_rt<Bv - 1>(x, s_mid);
+                if (++h >= nblocks) break;
+                fj = Bv + ctz64(h);
+                fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
+            } else {
+                fj = Bv + m - 1;
+                fs = ((gb >> (Bv + m)) & 1ull) ? -1 : 1;
+                net = true;
+                h += 1ull << m;
+            }
             continue;
         }
         P LA[Bv + 1], LB[Bv + 1];
@@ -639,6 +656,9 @@ __device__ __forceinline__ typename A::Acc walk_chunk_dual(Pol &pol, u64 q, int 
         if constexpr (Pol::kUnrolledDual) DualSteps<Pol, A, Bv, 0>::run(pol, x, LA, LB, blk, s_mid);
         else dual_block<Pol, A, Bv>(pol, x, LA, LB, blk, s_mid);
         A::blk_accumulate(mid, blk);
+        if (++h >= nblocks) break;
+        fj = Bv + ctz64(h);
+        fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
     }
     A::acc_merge(acc, mid);
     return acc;
@@ -660,18 +680,29 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
     // accumulator every 8 blocks (and at the end of the chunk)
     typename A::Blk mid = A::blk_zero();
     const u64 nblocks = 1ull << (K - Bv);
-    for (u64 h = 0; h < nblocks; ++h) {
+    u64 h = 0;
+    // The run-time flips of x (a block boundary's, a zero span's net flip)
+    // share one call site: in a generated kernel each site inlines the
+    // literal updates of every column.
+    int fj = -1, fs = 1;   // the flip due before block h (none at the chunk start)
+    bool net = false;      // it is a zero span's net flip, and block h's own flip follows
+    for (;;) {
+        if (fj >= 0) {
+            pol.flip_dyn(fj, x, fs);
+            if (net) {
+                net = false;
+                if (h >= nblocks) break;
+                fj = Bv + ctz64(h);
+                fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
+                continue;
+            }
+            QB = pol.chain_hi(fj, x);
+        }
         if (h != 0 && (h & 7) == 0) {
             A::acc_merge(acc, mid);
             mid = A::blk_zero();
         }
         const u64 gb = g0 + (h << Bv);
-        if (h != 0) {
-            const int j = Bv + ctz64(h);
-            const int s = ((gb >> (j + 1)) & 1ull) ? -1 : 1;
-            pol.flip_dyn(j, x, s);
-            QB = pol.chain_hi(j, x);
-        }
         const int s_mid = ((gb >> Bv) & 1ull) ? -1 : 1;
         // The vote runs every block, skip or not: it is also the point where
         // the warp reconverges after the data-driven loops of a flip.
@@ -680,10 +711,18 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
             // every product of this block (and of the widest zero span that
             // starts here) is zero; apply the span's net flip
             const int m = zero_span<Pol, Bv>(pol, h, K);
-            if (m == 0) pol.template flip_rt<Bv - 1>(x, s_mid);
-            else pol.flip_dyn(Bv + m - 1, x, ((gb >> (Bv + m)) & 1ull) ? -1 : 1);
             skipped += 1ull << m;
-            h += (1ull << m) - 1;
+            if (m == 0) {
+                pol.template flip_rt<Bv - 1>(x, s_mid);
+                if (++h >= nblocks) break;
+                fj = Bv + ctz64(h);
+                fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
+            } else {
+                fj = Bv + m - 1;
+                fs = ((gb >> (Bv + m)) & 1ull) ? -1 : 1;
+                net = true;
+                h += 1ull << m;
+            }
             continue;
         }
         P Q[Bv + 1];
@@ -703,6 +742,9 @@ __device__ __forceinline__ typename A::Acc walk_chunk_single(Pol &pol, u64 q, in
             BlockSteps<Pol, A, Bv, 1>::run(pol, x, Q, blk, s_mid);
         }
         A::blk_accumulate(mid, blk);
+        if (++h >= nblocks) break;
+        fj = Bv + ctz64(h);
+        fs = (((g0 + (h << Bv)) >> (fj + 1)) & 1ull) ? -1 : 1;
     }
     A::acc_merge(acc, mid);
     return acc;

@@ -77,6 +77,7 @@ struct GenericPol {
     static constexpr bool kDual = A::kProdIsX && NMAX <= 32;
     static constexpr bool kUnrolledDual = false;   // the pairs of a block are a rolled loop
     static constexpr bool kAbs = true;             // sum|terms| is always kept
+    static constexpr bool kZeroSpans = true;       // the two-state walk widens zero skips (core.cuh)
     typedef typename A::X X;
     typedef typename A::P P;
     typedef typename A::V V;

@@ -155,11 +155,12 @@ def test_generated_f64_walks(flags):
     check_f64(a, 9, [0, 3, 1000, (1 << 23 >> 9) - 1], flags=flags)
 
 
-@pytest.mark.parametrize("name", ["curtis54", "bcspwr02"])
+@pytest.mark.parametrize("name", ["curtis54", "bcspwr02", "mycielskian6"])
 def test_zero_spans_on_binary_table2_shapes(name):
     """Binary matrices with Table II's shapes, where almost every product is
     zero (Sec. VI-E): the walk skips whole aligned spans of blocks (up to a
-    whole 2^12-step chunk) and applies each span's net flip.  Every chunk's
+    whole 2^12-step chunk) and applies each span's net flip (mycielskian6's
+    kernel is built without spans and skips single blocks).  Every chunk's
     sum must still equal the oracle's over the same Gray range."""
     a = synth.table2_like(name)
     K = 12

@@ -250,6 +250,20 @@ def test_generated_block_length_follows_arithmetic_and_zeros():
         assert b == B and c >= B, (a.shape, a.dtype, b, c)
 
 
+def test_zero_spans_only_where_a_warp_can_share_zero_rows():
+    """Generated kernels widen zero skips into zero spans when most sampled
+    terms are zero and the pattern is sparse enough (density below 1/6) for
+    the six columns in which a warp's 32 chunks differ to leave rows
+    untouched; otherwise the span code is left out."""
+    def spans(a):
+        return "kZeroSpans = true" in A.codegen_source(a)
+    assert spans(synth.table2_like("curtis54")) and spans(synth.table2_like("bcspwr02"))
+    assert spans(synth.table2_like("d_ss"))
+    assert not spans(synth.table2_like("mycielskian6"))                                 # dense: lanes differ everywhere
+    assert not spans(synth.band_plus(48, 3, 2, seed=3, values="01"))                    # odd row sums: no zero terms
+    assert not spans(synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True))     # distinct reals
+
+
 def test_order_search_lowers_the_walk_cost_model():
     """The AUTO order search (FP64 walks of 2^30 steps and more) only accepts
     column swaps that lower the cost model of the scheme the walk runs; its
