@@ -81,3 +81,13 @@ def test_full_size_batch_sampled_and_alone_vs_mix():
             assert alone.value == res[i].value
         else:
             assert (alone.f64, alone.f64_lo) == (res[i].f64, res[i].f64_lo)
+
+
+def test_large_sparse_matrices_in_a_batch_match_the_row_dp():
+    """The same large sparse matrices as the serving test (n = 26..40), in one
+    batch with small ones, against the oracle's row-expansion DP."""
+    from tests.test_gpu_serving import check_against_row_dp, large_sparse_requests
+    mats = large_sparse_requests() + [it.a for it in synth.batch(count=40, seed=8) if it.n <= 20]
+    res = A.batch(mats)
+    for m, r in zip(mats, res):
+        check_against_row_dp(m, r)

@@ -85,3 +85,38 @@ def test_timeout_and_shutdown():
     s2 = A.Server()
     t2 = s2.submit(synth.single_er(36, 0.1, 6, values="f64"))
     s2.close()      # cancels the unfinished request and frees everything
+
+
+def large_sparse_requests():
+    """Sparse requests of n = 26..40 (ER p = 0.06..0.1 + diagonal), 0/1 and
+    (0,1] values, whose permanents the oracle's row-expansion DP (Eq. 1)
+    gives at once."""
+    out = []
+    for k, (n, p) in enumerate([(26, 0.1), (30, 0.1), (34, 0.08), (36, 0.08), (40, 0.06)]):
+        out.append(synth.single_er(n, p, 901 + k, values="01"))
+        out.append(synth.single_er(n, p, 951 + k, values="f64"))
+    return out
+
+
+def check_against_row_dp(m, r):
+    assert r.status == 0
+    if m.dtype == np.int64:
+        assert r.value == oracle.rowdp_int(m)
+    else:
+        want = float(oracle.rowdp(m))
+        n = m.shape[0]
+        assert abs(r.value - want) <= max(1e-9 * abs(want), 64 * n * 2.0 ** -53 * r.abs_term_sum), (n, r.value, want)
+
+
+def test_large_sparse_requests_match_the_row_dp():
+    """Served requests far beyond the oracle walk's reach on the CPU (up to 2^39
+    Gray steps), mixed with small ones: exact results equal the oracle's
+    row-expansion DP bit for bit, FP64 ones agree within 1e-9 or the rounding
+    bound of their sum of |terms|."""
+    big = large_sparse_requests()
+    small = [r.a for r in synth.serving_stream(rate=2000.0, duration=0.01, seed=6) if r.a.shape[0] <= 22][:10]
+    with A.Server() as s:
+        tickets = [s.submit(m) for m in big + small]
+        res = [s.poll(t, 120000) for t in tickets]
+    for m, r in zip(big + small, res):
+        check_against_row_dp(m, r)
