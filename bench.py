@@ -242,7 +242,7 @@ def extras(A, sh, a, first):
                                "generation and compilation per matrix (Sec. VI-F)"}
     # accuracy against the oracle
     golden = {}
-    for line in open(os.path.join(ROOT, "tests", "golden", "cfg2_n36.txt")):
+    for line in open(os.path.join(ROOT, "tests", "golden", "er36_f64_perm.txt")):
         if line.strip() and not line.startswith("#"):
             k, v = line.split()
             golden[k] = float(v)
@@ -252,14 +252,14 @@ def extras(A, sh, a, first):
     r01, rf = A.permanent(a01, stream=sh), A.permanent(af, stream=sh)
     out["accuracy"] = {
         "target": "exact results bit-identical, FP64 within 1e-9 relative to the oracle's permanent",
-        "cfg1_n24": {"exact_matches": r01.value == oracle_value(a01), "f64_rel_err": rel(rf.value, oracle_value(af)),
+        "er24_01_and_f64": {"exact_matches": r01.value == oracle_value(a01), "f64_rel_err": rel(rf.value, oracle_value(af)),
                      "f64_precision": "double-double" if rf.precision == 2 else "fp64"},
-        "cfg2_n36": {"f64_rel_err": rel(first.value, want2),
+        "er36_f64": {"f64_rel_err": rel(first.value, want2),
                      "kappa_sum_abs_terms_over_perm": golden["abs_terms"] / abs(want2),
-                     "reference": "oracle value stored in tests/golden/cfg2_n36.txt"},
-        "cfg4_batch_sampled": out["batch"].get("accuracy_vs_oracle"),
-        "cfg5_serving_sampled": out["serving"].get("accuracy_vs_oracle"),
-        "cfg3_n48": "whole 2^47-step exact walks: bench.py --workload cfg3 (profiles/cfg3_n48_full_permanent.md)"}
+                     "reference": "oracle value stored in tests/golden/er36_f64_perm.txt"},
+        "batch_sampled": out["batch"].get("accuracy_vs_oracle"),
+        "serving_sampled": out["serving"].get("accuracy_vs_oracle"),
+        "band48": "whole 2^47-step exact walks: bench.py --workload band48 (profiles/band48_whole_permanent.md)"}
     out["exact_roofline"] = exact_roofline(A, sh)
     out["cpu_fp64_baseline"] = cpu_fp64_baseline(a)
     out["table2"] = measure_table2(A)
@@ -270,12 +270,12 @@ def exact_roofline(A, sh):
     """The exact path against the integer issue roofline: counted integer
     multiply operations per Gray step (the ring-op cost model,
     perm_inspect_t.ring_ops_per_step) x steps / kernel time, over the IMAD
-    rate measured on this GPU: cfg1 (n=24 0/1, the plan the library picks) and
+    rate measured on this GPU: the n=24 0/1 ER matrix (the plan the library picks) and
     the n=48 band's generated exact kernel on a 2^30-step prefix."""
     from paper_2501_15126_gb300 import synth
     _, imad = A.issue_rates(sh)
     out = {"bound": "alu (IMAD)", "peak_imad_ops_per_s": imad}
-    for name, a, kw in (("cfg1_n24_01", synth.single_er(24, 0.2, 1, values="01"), {}),
+    for name, a, kw in (("er24_01", synth.single_er(24, 0.2, 1, values="01"), {}),
                         ("n48_band_01_prefix_2^30", synth.band_plus(48, 3, 2, seed=3, values="01"),
                          dict(g_lo=0, g_hi=1 << 30, engine=A.PERM_ENGINE_CODEGEN))):
         p = A.Plan(a, **kw)
@@ -591,7 +591,7 @@ def run_serving(args):
     return 0
 
 
-def run_cfg3(args):
+def run_band48(args):
     """The n=48 band workload in full (2^47 Gray steps per permanent), exact,
     through checkpointed slices: the band |i-j| <= 3 plus 2 off-band nonzeros
     per row (0/1) in the Algorithm 3 order and in the degree order -- the
@@ -612,7 +612,7 @@ def run_cfg3(args):
     out = {"workload": "n=48 band |i-j|<=3 + 2 off-band nonzeros per row, 0/1 values, seed 3 (and its band-only "
                        "sibling); whole 2^47-step walks, exact", "slice_log2": args.slice_log2, "runs": {}}
     for name, a, order in runs:
-        path = os.path.join(args.ckpt_dir, "cfg3_%s.ckpt" % name)
+        path = os.path.join(args.ckpt_dir, "band48_%s.ckpt" % name)
         t0 = time.time()
         st, r = A.checkpoint_run(a, path, slice_log2=args.slice_log2, max_slices=args.max_slices,
                                  ordering=order, engine=A.PERM_ENGINE_CODEGEN)
@@ -822,11 +822,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="single workload: only the headline (no batch, serving, accuracy, cold e2e, FP64 CPU baseline)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile", "cfg3", "ablation",
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving", "profile", "band48", "ablation",
                                                              "table2"])
-    ap.add_argument("--ckpt-dir", default="gpurun_out/cfg3_ckpt", help="cfg3: checkpoint files")
-    ap.add_argument("--slice-log2", type=int, default=40, help="cfg3: Gray indices per checkpointed slice (log2)")
-    ap.add_argument("--max-slices", type=int, default=0, help="cfg3: slices per run per call (0 = all)")
+    ap.add_argument("--ckpt-dir", default=os.path.join(tempfile.gettempdir(), "perm_band48_ckpt"),
+                    help="band48: checkpoint files")
+    ap.add_argument("--slice-log2", type=int, default=40, help="band48: Gray indices per checkpointed slice (log2)")
+    ap.add_argument("--max-slices", type=int, default=0, help="band48: slices per run per call (0 = all)")
     ap.add_argument("--profile-log2", type=int, default=30)
     ap.add_argument("--profile-exact", action="store_true")
     ap.add_argument("--profile-chunk-log2", type=int, default=0, help="profile: K (0 = the plan's choice)")
@@ -853,8 +854,8 @@ def main():
         return run_serving(args)
     if args.workload == "profile":
         return run_profile_case(args)
-    if args.workload == "cfg3":
-        return run_cfg3(args)
+    if args.workload == "band48":
+        return run_band48(args)
     if args.workload == "table2":
         return run_table2(args)
     if args.workload == "ablation":

@@ -3,7 +3,7 @@ oracle only (never the CUDA path).
 
     python tests/golden/make_golden.py [--threads T]
 
-cfg2_n36.txt: the n=36 ER (p=0.15, forced diagonal, (0,1] values, shuffled
+er36_f64_perm.txt: the n=36 ER (p=0.15, forced diagonal, (0,1] values, shuffled
 columns, seed 2) matrix's permanent by Algorithm 1 in long double over the
 full 2^35 Gray range, with the sum of |terms| (its conditioning).  Takes a few
 minutes on 8 x86-64 cores (80-bit long double there; 64-bit significand).
@@ -27,7 +27,7 @@ def main():
     t0 = time.time()
     perm, absum = oracle.nw_perm(a, threads=threads)
     dt = time.time() - t0
-    with open(os.path.join(HERE, "cfg2_n36.txt"), "w") as f:
+    with open(os.path.join(HERE, "er36_f64_perm.txt"), "w") as f:
         f.write("# n=36 ER p=0.15 + diagonal, (0,1] values, shuffled columns, seed 2 (synth.single_er)\n")
         f.write("# oracle.nw_perm: Algorithm 1 in long double (%d-bit significand), %d threads, %.0f s\n"
                 % (oracle.long_double_bits(), threads, dt))

@@ -66,7 +66,7 @@ def test_small_n_f64_matches_oracle(n, engine):
     assert rel_err(r.value, want) <= RTOL, (n, r.value, want)
 
 
-def test_cfg1_exact_and_f64():
+def test_er24_exact_and_f64():
     """n=24, ER p=0.2 + diagonal, 0/1 values: bit-exact; the same pattern with
     (0,1] values: FP64 within 1e-9."""
     a01 = synth.single_er(24, 0.2, 1, values="01")
@@ -228,7 +228,7 @@ def test_subrange_sums_add_up_to_the_permanent():
     assert rel_err(-2.0 * parts, A.permanent(af).value) < 1e-12
 
 
-def test_cfg2_subranges():
+def test_er36_subranges():
     """n=36, ER p=0.15 + diagonal, (0,1] values, shuffled columns: Gray sub-ranges
     anywhere in [0, 2^35), including ranges whose high bits are set."""
     a = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
@@ -238,7 +238,7 @@ def test_cfg2_subranges():
             subrange_check_f64(a, lo, lo + span, engine=engine)
 
 
-def test_cfg3_subranges_exact_and_f64():
+def test_band48_subranges_exact_and_f64():
     """n=48 band |i-j|<=3 + 2 off-band nonzeros per row, with the register/global split."""
     a01 = synth.band_plus(48, 3, 2, seed=3, values="01")
     af = synth.band_plus(48, 3, 2, seed=3, values="f64")
@@ -282,12 +282,12 @@ def test_band_only_sibling_full_walk_against_band_dp(engine):
         assert A.permanent(b01, engine=engine).value == oracle.band_dp_int(b01, 3)
 
 
-def test_cfg2_full_permanent_against_stored_oracle_value():
+def test_er36_full_permanent_against_stored_oracle_value():
     """The n=36 workload at full size, in the launch configuration bench.py
     times, against the oracle's full-range value stored in tests/golden."""
     import os
     vals = {}
-    for line in open(os.path.join(os.path.dirname(__file__), "golden", "cfg2_n36.txt")):
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "er36_f64_perm.txt")):
         if line.startswith("#") or not line.strip():
             continue
         k, v = line.split()

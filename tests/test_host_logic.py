@@ -107,8 +107,8 @@ def test_algorithm3_ordering_picks_min_unordered_degree():
                   [1, 1, 0, 1],
                   [0, 0, 1, 1]], dtype=np.int64)
     ins = A.inspect(a, ordering=A.PERM_ORDER_PAPER)
-    # round 1: min cdeg is column 1 (1 nonzero) -> row 2 ordered; cdeg[0]=2, cdeg[3]=2, cdeg[2]=2
-    # round 2: ties at 2 -> smallest index, column 0 -> rows 0, 1; cdeg[2]=1, cdeg[3]=1
+    # step 1: min cdeg is column 1 (1 nonzero) -> row 2 ordered; cdeg[0]=2, cdeg[3]=2, cdeg[2]=2
+    # step 2: ties at 2 -> smallest index, column 0 -> rows 0, 1; cdeg[2]=1, cdeg[3]=1
     # round 3: column 2 (1) -> row 3; round 4: column 3
     assert list(ins.col_order)[:4] == [1, 0, 2, 3]
     assert list(ins.row_order)[:4] == [2, 0, 1, 3]
@@ -220,11 +220,11 @@ def test_generated_fp64_kernel_picks_the_cheaper_chain():
     sparse ER matrix, where column 0 touches one row); PERM_FLAG_PAIRED_CHAIN
     forces the paired chain; exact kernels keep one chain."""
     band = synth.band_plus(48, 3, 2, seed=3, values="f64")
-    cfg2 = synth.single_er(36, 0.15, 2, values="f64")
+    er36 = synth.single_er(36, 0.15, 2, values="f64")
     sparse = synth.single_er(32, 0.05, 3, values="f64")
     assert "kDual = true" in A.codegen_source(band)
     assert "kDual = false" in A.codegen_source(band, flags=A.PERM_FLAG_PAIRED_CHAIN)
-    assert "kDual = true" in A.codegen_source(cfg2)
+    assert "kDual = true" in A.codegen_source(er36)
     assert "kDual = false" in A.codegen_source(sparse)
     assert "kDual = false" in A.codegen_source(synth.band_plus(48, 3, 2, seed=3, values="01"))   # exact: one chain
 
@@ -282,8 +282,8 @@ def test_order_search_lowers_the_walk_cost_model():
             assert auto.ops_per_step_walk < base
         assert A.inspect(a, ordering=A.PERM_ORDER_SEARCH).ops_per_step_walk == auto.ops_per_step_walk
     # the n=36 workload: 8.23 -> about 6.5 counted FP64 operations per step
-    cfg2 = A.inspect(cases[0][0])
-    assert cfg2.ordering == A.PERM_ORDER_SEARCH and cfg2.ops_per_step_walk < 7.0
+    er36 = A.inspect(cases[0][0])
+    assert er36.ordering == A.PERM_ORDER_SEARCH and er36.ops_per_step_walk < 7.0
     short = synth.single_er(24, 0.2, 1, values="01")
     assert A.inspect(short).ordering in (A.PERM_ORDER_DEGREE, A.PERM_ORDER_PAPER)
     exact_long = synth.single_er(34, 0.2, 5, values="01")   # exact walks keep the start order
