@@ -176,3 +176,15 @@ def test_zero_spans_on_the_d_ss_shape_in_fp64():
     K = 12
     top = (1 << (a.shape[0] - 1)) >> K
     check_f64(a, K, [0, 5, top // 3, top - 1], flags=A.PERM_FLAG_ABS_SUM)
+
+
+def test_zero_spans_in_a_two_state_fp64_kernel():
+    """A 0/1 ER matrix (n = 28, p = 0.1) walked in FP64: its generated kernel
+    runs two-state chains and zero spans; chunk sums within the rounding bound
+    of the oracle's."""
+    a = synth.single_er(28, 0.1, 3, values="01").astype(np.float64)
+    src = A.codegen_source(a, engine=A.PERM_ENGINE_CODEGEN)
+    assert "kDual = true" in src and "kZeroSpans = true" in src
+    K = 12
+    top = (1 << 27) >> K
+    check_f64(a, K, [0, 1, 5, top // 3, top - 1], flags=A.PERM_FLAG_ABS_SUM)

@@ -101,10 +101,12 @@ def test_whole_walk_of_the_bcspwr02_shape_against_the_row_dp():
     assert abs(rf.value - want) <= max(1e-9 * want, 64 * 49 * U * rf.abs_term_sum)
 
 
-def test_generic_two_state_walk_zero_spans_in_fp64():
-    """0/1 matrices walked in FP64 by the generic two-state kernel (the batch
-    and serving FP64 path), where most terms are zero: whole walks at chunk
-    lengths up to 2^16 (so spans reach whole chunks) equal the exact permanent,
+@pytest.mark.parametrize("engine", [A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN])
+def test_two_state_walk_zero_spans_in_fp64(engine):
+    """0/1 matrices walked in FP64 by the two-state walk (the generic kernel of
+    the batch and serving FP64 path; a generated kernel with two-state chains
+    and zero spans), where most terms are zero: whole walks at chunk lengths
+    up to 2^16 (so spans reach whole chunks) equal the exact permanent,
     sub-ranges match the oracle's partial sums, the skip fraction shows the
     spans at work, and the batch path gives the same values."""
     mats = [synth.single_er(28, 0.1, s, values="01") for s in (3, 4)] + [synth.band_plus(30, 1, 1, seed=2)]
@@ -113,15 +115,17 @@ def test_generic_two_state_walk_zero_spans_in_fp64():
         want = oracle.rowdp_int(a)
         af = a.astype(np.float64)
         for K in (8, 12, 16):
-            r = A.permanent(af, engine=A.PERM_ENGINE_GENERIC, chunk_log2=K)
+            r = A.permanent(af, engine=engine, chunk_log2=K)
             assert abs(r.value - want) <= 1e-9 * abs(want), (n, K, r.value, want)
         assert r.zero_skip_frac > 0.5, r.zero_skip_frac
         ao = in_plan_order(af)
         for lo in (0, 1 << 20, (1 << (n - 1)) - (1 << 18)):
             hi = lo + (1 << 18)
             s, sa = oracle.nw_range(ao, lo, hi, threads=16)
-            rs = A.permanent(af, g_lo=lo, g_hi=hi, engine=A.PERM_ENGINE_GENERIC, flags=A.PERM_FLAG_ABS_SUM)
+            rs = A.permanent(af, g_lo=lo, g_hi=hi, engine=engine, flags=A.PERM_FLAG_ABS_SUM)
             assert abs(rs.value - float(s)) <= 64 * n * U * float(sa) + 1e-300, (n, lo)
+    if engine != A.PERM_ENGINE_GENERIC:
+        return
     got = A.batch([m.astype(np.float64) for m in mats])
     for a, r in zip(mats, got):
         want = oracle.rowdp_int(a)
