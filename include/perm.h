@@ -157,8 +157,10 @@ typedef struct {
     int32_t flags;         /* PERM_FLAG_* bits                                             */
     double gr_ratio;       /* Algorithm 4 GRratio; 0 = the library's GB300 value           */
     uint64_t g_lo, g_hi;   /* Gray-index sub-range [g_lo, g_hi); both 0 = whole range.     */
-                           /*   Both ends must be multiples of 32.  A sub-range result is  */
-                           /*   the raw partial sum (see perm_result_t).                   */
+                           /*   Both ends must be multiples of 32 (g_hi may also be       */
+                           /*   2^(n-1)).  A sub-range result is the raw partial sum (see  */
+                           /*   perm_result_t); an empty one [g, g), g > 0, gives 0 with   */
+                           /*   steps = 0 and nothing launched.                            */
     int32_t timeout_ms;    /* device-side deadline for one compute: warps stop taking work */
                            /*   once the GPU clock passes it, and the call returns         */
                            /*   PERM_ERR_TIMEOUT (the context stays usable); 0 = none      */

@@ -286,6 +286,10 @@ perm_status_t plan_prepare(const perm_matrix_t *A, const perm_opts_t *opts_in, p
         }
         P.fold = max_row <= 127;
     }
+    // an empty sub-range [g, g) (g > 0; both ends 0 mean the whole walk) has
+    // the partial sum 0: nothing launches, and the ring width above stays
+    // the one a non-empty sub-range of this matrix reports
+    if (P.subrange && P.g_lo == P.g_hi) P.zero = true;
     P.ms_plan = now_ms() - t0;
     return PERM_OK;
 }

@@ -74,22 +74,51 @@ def finish_exact(total: int, n: int, words: int) -> int:
     return -v if (n - 1) % 2 else v
 
 
+def combine_shards(n: int, walk, words: int = 0, device="cpu"):
+    """One permanent from this rank's shard of the Gray range [0, 2^(n-1)):
+    `walk(lo, hi)` returns the shard's raw partial sum -- (hi, lo) doubles, or
+    `words` little-endian 64-bit words of the doubled exact sum modulo
+    2^(64 words) -- and an opaque record; one all_gather and the finishing step
+    give every rank the same value.  A rank whose shard is empty (more ranks
+    than 32-index units, tiny n) contributes zero without calling `walk`.
+    Returns (value, the record or None)."""
+    lo, hi = shard_range(1 << (n - 1), dist.get_world_size(), dist.get_rank())
+    if lo == hi:
+        part, rec = ([0] * words if words else (0.0, 0.0)), None
+    else:
+        part, rec = walk(lo, hi)
+    if words:
+        return finish_exact(combine_exact(list(part), device), n, words), rec
+    s_hi, s_lo = combine_f64(part[0], part[1], device)
+    f = 2.0 if n % 2 else -2.0          # 4 (n mod 2) - 2, Algorithm 1
+    return (s_hi + s_lo) * f, rec
+
+
 def permanent_sharded(a, device="cpu", **kw):
     """One permanent split across the ranks of the default process group:
     this rank walks its shard of the Gray range on its GPU through the C ABI
     (perm_plan_create + perm_compute with g_lo/g_hi), then one all_gather of
     the partial sums and the finishing step give every rank the same value.
-    Returns (value, this rank's Result)."""
+    Integer inputs walk one ring, 2^(64 w), on every rank (w from the
+    matrix's bound, as a sub-range of it takes by default), so the partial
+    sums add up.  Returns (value, this rank's Result, or None for an empty
+    shard)."""
+    import numpy as np
     from paper_2501_15126_gb300 import _abi as A
+    a = np.asarray(a)
     n = a.shape[0]
-    lo, hi = shard_range(1 << (n - 1), dist.get_world_size(), dist.get_rank())
-    r = A.permanent(a, g_lo=lo, g_hi=hi, **kw)
-    if r.vtype == A.PERM_I64:
-        words = [int(r.partial[i]) for i in range(r.exact_words)]
-        return finish_exact(combine_exact(words, device), n, r.exact_words), r
-    s_hi, s_lo = combine_f64(r.f64, r.f64_lo, device)
-    f = 2.0 if n % 2 else -2.0          # 4 (n mod 2) - 2, Algorithm 1
-    return (s_hi + s_lo) * f, r
+    words = 0
+    if np.issubdtype(a.dtype, np.integer):
+        words = kw.get("exact_words") or A.inspect(a).exact_words or 3
+        kw["exact_words"] = words
+
+    def walk(lo, hi):
+        r = A.permanent(a, g_lo=lo, g_hi=hi, **kw)
+        if words:
+            return [int(r.partial[i]) for i in range(words)], r
+        return (r.f64, r.f64_lo), r
+
+    return combine_shards(n, walk, words, device)
 
 
 def max_over_ranks(value: float, device="cpu") -> float:

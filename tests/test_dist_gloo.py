@@ -73,6 +73,76 @@ def test_two_rank_shards_combine_to_the_whole(world):
     assert len({(r[1], r[2], r[3]) for r in out}) == 1
 
 
+def tiny_worker(rank, world, port, q):
+    """combine_shards with oracle walks of tiny matrices: with more ranks than
+    32-index units some shards are empty, rank 0's included ([0, 0))."""
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2501_15126_gb300 import dist as pd
+        from paper_2501_15126_gb300 import synth
+        got = []
+        for n in (4, 6, 7, 8):
+            af = synth.single_er(n, 0.6, 30 + n, values="f64")
+            ai = synth.single_er(n, 0.6, 30 + n, values="01")
+            calls = []
+
+            def walk_f(lo, hi):
+                calls.append((lo, hi))
+                s, _ = oracle.nw_range(af, lo, hi)
+                return (s.hi, s.lo), (lo, hi)
+
+            def walk_i(lo, hi):
+                part = oracle.nw2_range(ai, lo, hi)
+                return [part & ((1 << 64) - 1), part >> 64], (lo, hi)
+
+            vf, rec = pd.combine_shards(n, walk_f, 0)
+            vi, _ = pd.combine_shards(n, walk_i, 2)
+            got.append((n, vf, vi, rec, calls))
+        q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_empty_shards_contribute_nothing():
+    """Three ranks, n = 4..8 (8 to 128 Gray indices: one to four 32-index
+    units), so some ranks own no indices; the combined permanent still equals
+    brute force (Eq. 1) on every rank, and an empty shard never walks."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    world = 3
+    procs = [ctx.Process(target=tiny_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    import oracle
+    from paper_2501_15126_gb300 import dist as pd
+    from paper_2501_15126_gb300 import synth
+    for k, n in enumerate((4, 6, 7, 8)):
+        af = synth.single_er(n, 0.6, 30 + n, values="f64")
+        ai = synth.single_er(n, 0.6, 30 + n, values="01")
+        want_f, want_i = float(oracle.brute(af)), oracle.brute_int(ai)
+        walked = []
+        for rank, got in out:
+            gn, vf, vi, rec, calls = got[k]
+            assert gn == n
+            assert abs(vf - want_f) <= 1e-12 * abs(want_f)
+            assert vi == want_i
+            lo, hi = pd.shard_range(1 << (n - 1), world, rank)
+            assert calls == ([] if lo == hi else [(lo, hi)])
+            assert rec == (None if lo == hi else (lo, hi))
+            walked += calls
+        assert sum(hi - lo for lo, hi in walked) == 1 << (n - 1)
+        assert any(pd.shard_range(1 << (n - 1), world, r)[1] == 0 for r in range(world)) == (n <= 7)
+
+
 def test_shard_range_covers_exactly():
     from paper_2501_15126_gb300 import dist as pd
     for total in (32, 1000, 1 << 20, (1 << 35)):

@@ -228,6 +228,24 @@ def test_subrange_sums_add_up_to_the_permanent():
     assert rel_err(-2.0 * parts, A.permanent(af).value) < 1e-12
 
 
+def test_empty_subrange_is_zero_and_launches_nothing():
+    """[g, g) with g > 0 a multiple of 32 is the sum over no Gray index: 0, no
+    steps (both ends 0 would mean the whole walk).  The exact path reports the
+    ring width of any other sub-range of the matrix, so such a partial sum
+    adds to the others (a rank with an empty shard)."""
+    a = synth.single_er(22, 0.3, 21, values="01")
+    af = synth.single_er(22, 0.3, 21, values="f64")
+    w = A.permanent(a, g_lo=0, g_hi=1 << 10).exact_words
+    for engine in (A.PERM_ENGINE_GENERIC, A.PERM_ENGINE_CODEGEN):
+        for g in (32, 1 << 20):
+            r = A.permanent(a, g_lo=g, g_hi=g, engine=engine)
+            assert (r.steps, r.partial_int, r.exact_words) == (0, 0, w)
+            rf = A.permanent(af, g_lo=g, g_hi=g, engine=engine)
+            assert (rf.steps, rf.f64, rf.f64_lo) == (0, 0.0, 0.0)
+    r = A.permanent_noalloc(a, g_lo=64, g_hi=64)
+    assert (r.steps, r.partial_int, r.exact_words) == (0, 0, w)
+
+
 def test_er36_subranges():
     """n=36, ER p=0.15 + diagonal, (0,1] values, shuffled columns: Gray sub-ranges
     anywhere in [0, 2^35), including ranges whose high bits are set."""
