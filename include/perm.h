@@ -377,6 +377,18 @@ perm_status_t perm_alg2_launches(int64_t tau, int32_t n, int64_t *start, int64_t
 perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opts, char *buf, int64_t cap,
                                   int64_t *len);
 
+/* The matrix image that the precompiled generic kernels read for A (for
+   inspection; the layout of Sec. III's sparse format as the kernels keep
+   it: column masks over row slots, group and S_m boundaries, the
+   Nijenhuis-Wilf start values of Algorithm 1 by slot, then the values of
+   the ordered columns 0..n-2).  Copies at most cap bytes to buf and sets
+   *len to the image size, *nmax to its NMAX bucket (16, 32 or 48), *kind to
+   its kernel family (0 FP64, 1 double-double, else 2 limbs + fold) and
+   *abs_shift to the scale of its sum of |terms|.  Needs no GPU.  Errors:
+   those of perm_plan_create's validation; SIZE for n > 48. */
+perm_status_t perm_generic_image(const perm_matrix_t *A, const perm_opts_t *opts, void *buf, int64_t cap,
+                                 int64_t *len, int32_t *nmax, int32_t *kind, int32_t *abs_shift);
+
 /* Measures this GPU's FP64 (DFMA) and 32-bit IMAD issue rates in lane
    operations per second with two short probe kernels on `stream` (8
    independent chains per thread, 8 blocks of 256 threads per SM).  These are

@@ -108,6 +108,8 @@ SIGNATURES = [
                                    ctypes.POINTER(c_i64), c_i32, ctypes.POINTER(c_i32)]),
     ("perm_codegen_source", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), ctypes.c_char_p, c_i64,
                                     ctypes.POINTER(c_i64)]),
+    ("perm_generic_image", c_i32, [ctypes.POINTER(Matrix), ctypes.POINTER(Opts), c_vp, c_i64, ctypes.POINTER(c_i64),
+                                   ctypes.POINTER(c_i32), ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
     ("perm_status_string", ctypes.c_char_p, [c_i32]),
     ("perm_last_error", ctypes.c_char_p, []),
     ("perm_device_available", c_i32, []),
@@ -267,6 +269,19 @@ def codegen_source(a, **kw) -> str:
     check(lib().perm_codegen_source(ctypes.byref(m.c), ctypes.byref(o), buf, n.value + 1, ctypes.byref(n)),
           "codegen")
     return buf.value.decode()
+
+
+def generic_image(a, **kw):
+    """perm_generic_image: (image bytes, NMAX bucket, kernel family, abs_shift)."""
+    m = a if isinstance(a, CSRMatrix) else CSRMatrix(a)
+    o = opts(**kw)
+    n, nmax, kind, shift = c_i64(), c_i32(), c_i32(), c_i32()
+    check(lib().perm_generic_image(ctypes.byref(m.c), ctypes.byref(o), None, 0, ctypes.byref(n), ctypes.byref(nmax),
+                                   ctypes.byref(kind), ctypes.byref(shift)), "perm_generic_image")
+    buf = ctypes.create_string_buffer(n.value)
+    check(lib().perm_generic_image(ctypes.byref(m.c), ctypes.byref(o), buf, n.value, ctypes.byref(n), None, None,
+                                   None), "perm_generic_image")
+    return buf.raw[: n.value], nmax.value, kind.value, shift.value
 
 
 def issue_rates(stream: int = 0):

@@ -12,10 +12,14 @@
 // files in parallel.
 #pragma once
 
+// (The host emulation tests compile the walk part of this file as host C++;
+// they leave out the CUDA runtime and the launchers.)
+#ifndef PERM_HOST_EMULATION
 #include <cuda_runtime.h>
 
-#include "core.cuh"
 #include "kernels.hpp"
+#endif
+#include "core.cuh"
 
 #ifndef PERM_GENERIC_B
 #define PERM_GENERIC_B 5
@@ -556,6 +560,7 @@ __global__ void __launch_bounds__(256) k_direct_generic(const DevMat<NMAX, typen
 
 }  // namespace pk
 
+#ifndef PERM_HOST_EMULATION
 namespace perm {
 
 template <int NMAX, class A>
@@ -604,6 +609,7 @@ static GenericFns make_fns() {
 }
 
 }  // namespace perm
+#endif  // PERM_HOST_EMULATION
 
 // Defines perm::generic_fns_<NAME>(nmax) for one arithmetic.
 #define PERM_GENERIC_UNIT(NAME, ARITH)                                   \

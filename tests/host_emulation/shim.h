@@ -23,6 +23,7 @@ using std::max;
 using std::min;
 
 struct perm_dim3 { unsigned x, y, z; };
+struct uint4 { unsigned x, y, z, w; };
 static perm_dim3 threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0}, blockDim = {32, 1, 1}, gridDim = {1, 1, 1};
 
 template <class T> inline T __shfl_sync(unsigned, T v, int) { return v; }

@@ -188,3 +188,19 @@ def test_zero_spans_in_a_two_state_fp64_kernel():
     K = 12
     top = (1 << 27) >> K
     check_f64(a, K, [0, 1, 5, top // 3, top - 1], flags=A.PERM_FLAG_ABS_SUM)
+
+
+@pytest.mark.parametrize("values", ["01", "f64"])
+def test_largest_size_n64(values):
+    """n = 64, the largest size the library takes (Gray indices up to 2^63 - 1,
+    a 192-bit ring on the exact path): an ER p = 0.08 + diagonal matrix, with
+    chunks at the start, on both sides of bit 62 of the Gray index, and the
+    very last chunk, against the oracle's sums over the same ranges."""
+    a = synth.single_er(64, 0.08, 64, values=values)
+    K = 12
+    top = (1 << 63) >> K
+    chunks = [0, 1, top // 2 - 1, top // 2, top - 2, top - 1]
+    if values == "01":
+        check_exact(a, K, chunks)
+    else:
+        check_f64(a, K, chunks, flags=A.PERM_FLAG_ABS_SUM)
