@@ -309,7 +309,18 @@ perm_status_t choose_launch(perm_plan_s &P, int block_log2, int blocks_per_sm, i
         // chunks of at least 2^(B+3) steps so the start vector stays a small cost
         const double want_tasks = 64.0 * (double)resident_warps;   // keeps the last round of tasks short
         K = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * want_tasks)));
-        K = std::max(K, block_log2 + 3);
+        int k_floor = block_log2 + 3;
+        if (P.arith != 0) {
+            // an exact walk too short to give every resident warp a task at that
+            // length takes chunks down to 2^(B+1) (its start vector is a few
+            // integer adds per column): the n=24 0/1 walk, 2^23 steps, takes
+            // 0.081 ms at 2^6-step chunks against 0.132 ms at 2^8, where 72 % of
+            // the warps had no task.  FP64 walks keep 2^(B+3) (the same matrix
+            // in FP64: 0.220 ms at 2^8, 0.228 at 2^6).
+            const int fill = floor_log2((uint64_t)std::max(1.0, (double)len / (32.0 * (double)resident_warps)));
+            k_floor = std::max(block_log2 + 1, std::min(k_floor, fill));
+        }
+        K = std::max(K, k_floor);
     } else {
         K = std::max(K, block_log2);   // a chunk holds whole blocks
     }
@@ -360,7 +371,8 @@ static void codegen_layout(perm_plan_s &P) {
     // must leave rows untouched, i.e. touch fewer than n rows on average
     // (density below 1/6).  Elsewhere the span code only costs registers (the
     // mycielskian6 shape, density 0.21: 255 instead of 128, 16 % slower).
-    P.zero_heavy = zero_term_fraction(P.m, P.L.col_order, 1024) > 0.25;
+    P.zero_frac = zero_term_fraction(P.m, P.L.col_order, 1024);
+    P.zero_heavy = P.zero_frac > 0.25;
     int nnz = 0;
     for (int i = 0; i < n; ++i) nnz += __builtin_popcountll(P.m.rowmask[i]);
     P.zero_spans = P.zero_heavy && 6 * nnz < n * n;
@@ -897,6 +909,23 @@ perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opt
         std::memcpy(buf, src.data(), nb);
         buf[nb] = 0;
     }
+    return PERM_OK;
+}
+
+perm_status_t perm_generic_image(const perm_matrix_t *A, const perm_opts_t *opts, void *buf, int64_t cap,
+                                 int64_t *len, int32_t *nmax, int32_t *kind, int32_t *abs_shift) {
+    perm_plan_s P;
+    perm_status_t st = plan_prepare(A, opts, P);
+    if (st != PERM_OK) return st;
+    if (P.m.n > 48) return fail(PERM_ERR_SIZE, "generic kernels cover n <= 48");
+    const int nm = nmax_bucket(P.m.n);
+    std::vector<unsigned char> img;
+    build_devmat(P.m, P.L, P.img_kind(), nm, img);
+    if (len) *len = (int64_t)img.size();
+    if (nmax) *nmax = nm;
+    if (kind) *kind = P.kind();
+    if (abs_shift) *abs_shift = P.abs_shift;
+    if (buf && cap > 0) std::memcpy(buf, img.data(), std::min<size_t>((size_t)cap, img.size()));
     return PERM_OK;
 }
 

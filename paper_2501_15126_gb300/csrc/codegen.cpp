@@ -45,11 +45,21 @@ namespace {
 // start (run-time flip, chain rebuild, vote) is then spread over more steps
 // (the n=36 FP64 walk: 370.9 ms at 2^5, 365.5 at 2^6, 361.5 at 2^7), and
 // their compile time grows little (0.64 -> 0.76 s).  Exact walks keep 2^5: at
-// 2^6 their NVRTC time grows by half and some need all 255 registers.  So
-// do FP64 walks where most terms are zero: their zero skip starts at a block
-// (the d_ss shape: 1.66e12 Gray steps/s at 2^5, 0.98e12 at 2^7).
+// 2^6 their NVRTC time grows by half and some need all 255 registers, and at
+// 2^4 the n=48 band walk is 19 % slower (5.95 against 5.00 ms per 2^30
+// steps).  FP64 walks where most terms are zero keep 2^5 too: their zero skip
+// starts at a block (the d_ss shape: 1.66e12 Gray steps/s at 2^5, 0.98e12 at
+// 2^7).  Exact walks where nearly every term is zero (over 95 % of the
+// sampled ones) but without zero spans (a warp's lanes rarely share a zero
+// row, so only single blocks are skipped, where every lane's products are
+// zero at once) take 2^4: a finer skip and half the unrolled body (the
+// mycielskian6 shape, 99.6 % zero terms: 235 against 306 ms per 2^36 steps,
+// 43 % of the blocks skipped against 38 %).  The n=48 band, 74 % zero terms,
+// skips no block and keeps 2^5.
 constexpr int kCodegenBlockLog2F64 = 7;
+constexpr int kCodegenBlockLog2ZeroHeavy = 5;
 constexpr int kCodegenBlockLog2Exact = 5;
+constexpr int kCodegenBlockLog2ZeroBlocks = 4;
 constexpr int kCodegenBlock = 256;
 
 // ------------------------------------------------------------------ driver API via the runtime
@@ -542,7 +552,8 @@ constexpr size_t kCacheMax = 512;
 bool codegen_no_fold() { return no_fold_env(); }
 
 int codegen_block_log2(const perm_plan_s &P) {
-    return P.arith == 0 && !P.zero_heavy ? kCodegenBlockLog2F64 : kCodegenBlockLog2Exact;
+    if (P.arith == 0) return P.zero_heavy ? kCodegenBlockLog2ZeroHeavy : kCodegenBlockLog2F64;
+    return P.zero_frac > 0.95 && !P.zero_spans ? kCodegenBlockLog2ZeroBlocks : kCodegenBlockLog2Exact;
 }
 
 std::string codegen_source(const perm_plan_s &P) {

@@ -51,6 +51,7 @@ struct perm_plan_s {
     bool dd = false;          // FP64 input walked in double-double arithmetic
     bool pure_reg = false;    // codegen: a full product of all n rows every step (CodeGen-PureReg)
     bool zero_heavy = false;  // codegen: most sampled terms have a zero factor (FP64: shorter blocks)
+    double zero_frac = 0.0;   // codegen: fraction of sampled terms with a zero factor
     bool zero_spans = false;  // codegen: the kernel widens zero skips into zero spans (core.cuh)
     bool want_abs = true;     // FP64 walks: accumulate sum|terms| (generated kernels: see codegen_layout)
     int abs_shift = 0;        // FP64 / double-double: sum|terms| is accumulated as sum|terms| 2^-abs_shift

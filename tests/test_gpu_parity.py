@@ -269,6 +269,21 @@ def test_band48_subranges_exact_and_f64():
     subrange_check_exact(a01, 1 << 30, (1 << 30) + span, engine=A.PERM_ENGINE_GENERIC)
 
 
+@pytest.mark.parametrize("values", ["01", "f64"])
+def test_largest_size_n64_subranges(values):
+    """n = 64, the largest size the library takes (Gray indices up to
+    2^63 - 1; above n = 48 only the generated kernels run): sub-ranges at the
+    start, across bit 62 of the Gray index and at the very end of the walk,
+    against the oracle."""
+    a = synth.single_er(64, 0.08, 64, values=values)
+    span, top = 1 << 20, 1 << 63
+    for lo in (0, (top >> 1) - span // 2, top - span):
+        if values == "01":
+            subrange_check_exact(a, lo, lo + span)
+        else:
+            subrange_check_f64(a, lo, lo + span)
+
+
 def test_three_level_placement_registers_shared_global():
     """The n=48 band workload with x in three tiers (Sec. V's split, carried to
     shared memory as Sec. VIII proposes): 20 rows in registers, 12 or 28 in
