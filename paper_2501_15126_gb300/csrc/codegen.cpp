@@ -108,15 +108,25 @@ std::string cu_err(CUresult r) {
 
 // ------------------------------------------------------------------ source emission
 // Resident 256-thread blocks per SM that the generated kernel is compiled for
-// (its register budget: 2 -> 128 registers, 3 -> 85).  PERM_CODEGEN_MIN_BLOCKS
-// overrides the default of 2.
-int codegen_min_blocks(const perm_plan_s &) {
+// (its register budget: 1 -> 255 registers, 2 -> 128, 3 -> 85).  FP64 walks
+// of 2^30 steps and more (those the automatic engine generates kernels for)
+// take one block: eight warps per SM keep the FP64 pipe as busy as sixteen,
+// and 255 registers hold x and both chains without spilling (the n=36
+// workload: 224 registers, no spills, 359.9 ms per permanent against 361.8 ms
+// at 128 registers with 152 bytes of spills; the bcsstk01 and mesh1e1
+// shapes 1.1 and 1.4 % faster, kernels that fit 128 registers unchanged).
+// Shorter FP64 walks keep two blocks (an n=28 walk, 2^27 steps: 2.6 %
+// slower with half the warps to share its tasks), and so do exact walks,
+// which are bound by instruction issue and need the warps (the n=48 band:
+// 5.86 ms at one block against 5.00 at two).  CodeGen-PureReg keeps two
+// blocks, as measured in the ablation.  PERM_CODEGEN_MIN_BLOCKS overrides.
+int codegen_min_blocks(const perm_plan_s &P) {
     const char *e = std::getenv("PERM_CODEGEN_MIN_BLOCKS");
     if (e) {
         const int v = std::atoi(e);
         if (v >= 1 && v <= 8) return v;
     }
-    return 2;
+    return P.arith == 0 && !P.pure_reg && P.len() >= (1ull << 30) ? 1 : 2;
 }
 // PERM_CODEGEN_NO_FOLD=1: exact kernels multiply every row into the ring on
 // its own (no 32-bit folding), as they did before folding was introduced.
@@ -694,7 +704,7 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     perm_status_t st = compile_and_load(src, ce, err, P.xs_bytes());
     if (st != PERM_OK) return st;
     const bool fixed_budget = std::getenv("PERM_CODEGEN_MIN_BLOCKS") != nullptr;
-    if (ce.local_bytes > kMaxLocalFrame && !fixed_budget) {
+    if (ce.local_bytes > kMaxLocalFrame && !fixed_budget && codegen_min_blocks(P) > 1) {
         if (driver().moduleUnload) driver().moduleUnload(ce.module);
         ce = CacheEntry();
         Emitter e1(P, 1);
