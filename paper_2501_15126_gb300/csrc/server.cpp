@@ -60,6 +60,20 @@ constexpr size_t kQueueMax = 1 << 20;
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Makes `dev` current for a scope and restores the caller's device after it:
+// perm_server_create and perm_submit run on the caller's thread, whose
+// current device is the caller's business.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 struct Request {
     uint64_t ticket = 0;
     std::unique_ptr<perm_plan_s> P;
@@ -173,9 +187,8 @@ struct perm_server_s {
 
     static int family_index(int nmax, int kind) { return (nmax / 16 - 1) * 14 + kind; }
 
-    perm_status_t init_device() {
-        cudaError_t e = cudaSetDevice(device);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    perm_status_t init_device() {   // on the creating thread, with `device` current
+        cudaError_t e;
         if ((e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamCreate");
         for (int i = 0; i < kStreams; ++i)
@@ -202,7 +215,7 @@ struct perm_server_s {
     perm_status_t ensure_family(int fi, int nmax, int kind) {
         Family &F = fam[fi];
         if (F.ready) return PERM_OK;
-        cudaSetDevice(device);
+        DeviceScope scope(device);
         F.nmax = nmax;
         F.kind = kind;
         F.arith = ((kind >> 1) + 1) / 2;
@@ -682,6 +695,12 @@ perm_status_t perm_server_create(const perm_server_opts_t *opts, perm_server_t *
     if (s->opts.precision < PERM_PREC_AUTO || s->opts.precision > PERM_PREC_DD) return fail(PERM_ERR_ARG, "bad precision");
     s->device = s->opts.device;
     s->step_budget = s->opts.step_budget > 0 ? s->opts.step_budget : 1.5e11;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || s->device < 0 || s->device >= ndev) {
+        cudaGetLastError();
+        return fail(ndev > 0 ? PERM_ERR_ARG : PERM_ERR_CUDA, "no such CUDA device");
+    }
+    DeviceScope scope(s->device);
     perm_status_t st = s->init_device();
     if (st != PERM_OK) { s->release_family_resources(); return st; }
     s->thread = std::thread([p = s.get()] { p->loop(); });
@@ -772,7 +791,10 @@ void perm_server_destroy(perm_server_t s) {
     }
     s->cv_work.notify_all();
     if (s->thread.joinable()) s->thread.join();
-    s->release_family_resources();
+    {
+        DeviceScope scope(s->device);
+        s->release_family_resources();
+    }
     delete s;
 }
 

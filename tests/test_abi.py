@@ -61,3 +61,17 @@ def test_bad_arguments_fail_without_a_gpu():
     assert L.perm_plan_create(ctypes.byref(big.c), None, ctypes.byref(h)) == A.PERM_ERR_SIZE
     r = A.Result()
     assert L.perm_compute_noalloc(ctypes.byref(big.c), None, None, ctypes.byref(r)) == A.PERM_ERR_SIZE
+
+
+def test_server_create_reports_a_missing_device():
+    """perm_server_create checks the device ordinal before touching it: without
+    a GPU it fails with CUDA, with one an ordinal past the last device gives ARG;
+    neither starts a thread or leaks a handle."""
+    L = A.lib()
+    h = ctypes.c_void_p()
+    o = A.ServerOpts()
+    o.device = 7 if L.perm_device_available() else 0
+    st = L.perm_server_create(ctypes.byref(o), ctypes.byref(h))
+    assert st == (A.PERM_ERR_ARG if L.perm_device_available() else A.PERM_ERR_CUDA)
+    assert not h.value
+    assert b"device" in L.perm_last_error()
