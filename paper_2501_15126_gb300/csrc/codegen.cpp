@@ -600,17 +600,24 @@ perm_status_t compile_and_load(const std::string &src, CacheEntry &ce, std::stri
     nvrtcDestroyProgram(&prog);
     cudaFree(nullptr);   // make the primary context current on this thread
     CUresult cr = d.moduleLoadData(&ce.module, cubin.data());
-    if (cr != CUDA_SUCCESS) { err = "cuModuleLoadData: " + cu_err(cr); return PERM_ERR_CUDA; }
+    if (cr != CUDA_SUCCESS) { ce.module = nullptr; err = "cuModuleLoadData: " + cu_err(cr); return PERM_ERR_CUDA; }
+    // a loaded module that fails a later step is unloaded, not leaked
+    auto unload_fail = [&](const char *what) {
+        err = std::string(what) + ": " + cu_err(cr);
+        if (d.moduleUnload) d.moduleUnload(ce.module);
+        ce = CacheEntry();
+        return PERM_ERR_CUDA;
+    };
     cr = d.moduleGetFunction(&ce.function, ce.module, "perm_walk");
-    if (cr != CUDA_SUCCESS) { err = "cuModuleGetFunction: " + cu_err(cr); return PERM_ERR_CUDA; }
+    if (cr != CUDA_SUCCESS) return unload_fail("cuModuleGetFunction");
     d.funcGetAttribute(&ce.regs, CU_FUNC_ATTRIBUTE_NUM_REGS, ce.function);
     d.funcGetAttribute(&ce.local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, ce.function);
     if (smem > 48 * 1024) {
         cr = d.funcSetAttribute(ce.function, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
-        if (cr != CUDA_SUCCESS) { err = "cuFuncSetAttribute: " + cu_err(cr); return PERM_ERR_CUDA; }
+        if (cr != CUDA_SUCCESS) return unload_fail("cuFuncSetAttribute");
     }
     cr = d.occupancy(&ce.blocks_per_sm, ce.function, kCodegenBlock, smem);
-    if (cr != CUDA_SUCCESS) { err = "occupancy: " + cu_err(cr); return PERM_ERR_CUDA; }
+    if (cr != CUDA_SUCCESS) return unload_fail("occupancy");
     return PERM_OK;
 }
 
@@ -685,9 +692,13 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     P.cg.block = kCodegenBlock;
     P.cg.block_log2 = codegen_block_log2(P);
     const bool use_cache = !(P.opts.flags & PERM_FLAG_NO_KERNEL_CACHE);
+    // a module belongs to one device's context: the cache key names the device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = -1; }
+    const std::string key = "device " + std::to_string(dev) + "\n" + src;
     if (use_cache) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
-        auto it = g_cache.find(src);
+        auto it = g_cache.find(key);
         if (it != g_cache.end()) {
             P.cg.module = it->second.module;
             P.cg.function = it->second.function;
@@ -729,8 +740,9 @@ perm_status_t codegen_build(perm_plan_s &P, std::string &err) {
     P.ms_compile = now_ms() - t0;
     if (use_cache) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
-        if (g_cache.size() < kCacheMax) g_cache.emplace(src, ce);
-        else P.cg.owned = true;
+        // another thread may have cached the same kernel meanwhile: this
+        // module then stays with the plan
+        if (g_cache.size() >= kCacheMax || !g_cache.emplace(key, ce).second) P.cg.owned = true;
     } else {
         P.cg.owned = true;
     }
