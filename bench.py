@@ -403,7 +403,7 @@ def run_ours(args):
                  "ordering": first.ordering},
         "imad_rate_measured": imad_rate,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the CPU baseline: rank 0 at N=1 only
         line["cpu_baseline"] = cpu_baseline(a, args.cpu_seconds)
     if world == 1 and not args.no_extras:
         line.update(extras(A, sh, a, first))
