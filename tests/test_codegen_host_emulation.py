@@ -204,3 +204,20 @@ def test_largest_size_n64(values):
         check_exact(a, K, chunks)
     else:
         check_f64(a, K, chunks, flags=A.PERM_FLAG_ABS_SUM)
+
+
+def test_headline_matrix_with_x_in_three_tiers_and_pure_reg():
+    """The n=36 workload (ER p = 0.15 + diagonal, (0,1], shuffled columns) in
+    FP64: the two-state kernel with x split over registers, shared memory and
+    global memory (18 + 8 + 10 rows: asking for 12 register rows gives the
+    18 that the unrolled 2^7-step block reaches), and the CodeGen-PureReg kernel (every
+    row in registers, a full product every step); chunks at the start, in the
+    middle and at the end of the walk."""
+    a = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
+    K = 12
+    top = (1 << 35) >> K
+    chunks = [0, 1, top // 2 + 3, top - 1]
+    src = A.codegen_source(a, reg_rows=12, shared_rows=8, flags=A.PERM_FLAG_ABS_SUM)
+    assert "reg_rows(k)=18 " in src and "xs[" in src and "xg[" in src
+    check_f64(a, K, chunks, reg_rows=12, shared_rows=8, flags=A.PERM_FLAG_ABS_SUM)
+    check_f64(a, K, chunks, flags=A.PERM_FLAG_PURE_REG | A.PERM_FLAG_ABS_SUM)
