@@ -75,3 +75,29 @@ def test_server_create_reports_a_missing_device():
     assert st == (A.PERM_ERR_ARG if L.perm_device_available() else A.PERM_ERR_CUDA)
     assert not h.value
     assert b"device" in L.perm_last_error()
+
+
+@pytest.mark.skipif(A.lib().perm_device_available() != 0, reason="shows that no device is touched")
+def test_zero_permanents_and_empty_ranges_launch_nothing():
+    """A matrix without a perfect matching (an empty row, or rows that share
+    too few columns) has permanent 0, and an empty Gray sub-range [g, g) the
+    partial sum 0: plan, compute and destroy run here, on a machine without a
+    GPU, which shows that nothing is launched or allocated on a device."""
+    import numpy as np
+    from paper_2501_15126_gb300 import synth
+    empty_row = np.ones((6, 6), dtype=np.int64)
+    empty_row[2, :] = 0
+    hall = np.zeros((5, 5))
+    hall[:, :2] = 0.5          # five rows, two columns between them: no matching
+    hall[0, :] = 1.0
+    for a in (empty_row, hall, synth.ones(10) * np.tri(10, k=-1, dtype=np.int64)):
+        r = A.permanent(a)
+        assert (r.value, r.steps, r.status) == (0, 0, A.PERM_OK)
+    a = synth.single_er(20, 0.3, 4, values="01")
+    w = A.inspect(a).exact_words
+    r = A.permanent(a, g_lo=64, g_hi=64)
+    assert (r.partial_int, r.steps, r.exact_words) == (0, 0, w)
+    r = A.permanent(synth.single_er(20, 0.3, 4, values="f64"), g_lo=1 << 10, g_hi=1 << 10)
+    assert (r.f64, r.f64_lo, r.steps) == (0.0, 0.0, 0)
+    res = A.batch([empty_row, hall])
+    assert [x.value for x in res] == [0, 0]

@@ -232,9 +232,10 @@ def test_generated_fp64_kernel_picks_the_cheaper_chain():
 def test_generated_block_length_follows_arithmetic_and_zeros():
     """Generated kernels unroll 2^7-step blocks for FP64 walks and 2^5 for exact
     ones, and for FP64 walks where most terms have a zero factor (repeated
-    values, Sec. VI-E), so that their zero skip starts at 2^5 steps.  The
-    FP64 kernel's split keeps every row reached inside a block in registers
-    (c >= B)."""
+    values, Sec. VI-E), so that their zero skip starts at 2^5 steps; exact
+    walks whose sampled terms are over 95 % zero but that get no zero spans
+    skip single blocks only, and unroll 2^4.  The kernel's split keeps every
+    row reached inside a block in registers (c >= B)."""
     import re
 
     def header(a, **kw):
@@ -245,6 +246,8 @@ def test_generated_block_length_follows_arithmetic_and_zeros():
                  (synth.table2_like("d_ss"), 5),
                  (synth.table2_like("curtis54").astype(np.float64), 5),
                  (synth.table2_like("curtis54"), 5),
+                 (synth.table2_like("mycielskian6"), 4),
+                 (synth.single_er(24, 0.2, 1, values="01"), 4),
                  (synth.band_plus(48, 3, 2, seed=3, values="01"), 5)]:
         c, b = header(a)
         assert b == B and c >= B, (a.shape, a.dtype, b, c)
@@ -260,7 +263,7 @@ def test_zero_spans_only_where_a_warp_can_share_zero_rows():
     assert spans(synth.table2_like("curtis54")) and spans(synth.table2_like("bcspwr02"))
     assert spans(synth.table2_like("d_ss"))
     assert not spans(synth.table2_like("mycielskian6"))                                 # dense: lanes differ everywhere
-    assert not spans(synth.band_plus(48, 3, 2, seed=3, values="01"))                    # odd row sums: no zero terms
+    assert not spans(synth.band_plus(48, 3, 2, seed=3, values="01"))                    # density above 1/6
     assert not spans(synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True))     # distinct reals
 
 
@@ -327,3 +330,21 @@ def test_cost_models_match_a_step_by_step_count():
         one, two = _schedule_counts(a, ins)
         assert abs(ins.ops_per_step - one) < 1e-9 * one, (ins.ops_per_step, one)
         assert abs(ins.ops_per_step_walk - two) < 1e-9 * two, (ins.ops_per_step_walk, two)
+
+
+def test_register_budget_of_generated_kernels():
+    """FP64 walks of 2^30 steps and more are built for one 256-thread block
+    per SM (up to 255 registers: x and both chains without spills), shorter
+    FP64 walks, exact walks and CodeGen-PureReg for two (128 registers)."""
+    import re
+
+    def blocks(a, **kw):
+        return int(re.search(r"__launch_bounds__\(256, (\d)\)", A.codegen_source(a, **kw)).group(1))
+    a36 = synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True)
+    assert blocks(a36) == 1
+    assert blocks(a36, g_lo=0, g_hi=1 << 30) == 1
+    assert blocks(a36, g_lo=0, g_hi=1 << 29) == 2
+    assert blocks(a36, flags=A.PERM_FLAG_PURE_REG) == 2
+    assert blocks(synth.single_er(28, 0.3, 6, values="f64")) == 2                   # 2^27 steps
+    assert blocks(synth.band_plus(48, 3, 2, seed=3, values="01")) == 2                # exact
+    assert blocks(synth.band_plus(48, 3, 2, seed=3, values="f64")) == 1
