@@ -378,10 +378,11 @@ perm_status_t perm_codegen_source(const perm_matrix_t *A, const perm_opts_t *opt
                                   int64_t *len);
 
 /* The matrix image that the precompiled generic kernels read for A (for
-   inspection; the layout of Sec. III's sparse format as the kernels keep
-   it: column masks over row slots, group and S_m boundaries, the
-   Nijenhuis-Wilf start values of Algorithm 1 by slot, then the values of
-   the ordered columns 0..n-2).  Copies at most cap bytes to buf and sets
+   inspection).  Sec. III names the sparse A and x as the two data
+   structures the walk touches; this is A as those kernels keep it in
+   shared memory, with x's start values: column masks over row slots, group
+   and S_m boundaries, the Nijenhuis-Wilf start values of Algorithm 1 by
+   slot, then the values of the ordered columns 0..n-2.  Copies at most cap bytes to buf and sets
    *len to the image size, *nmax to its NMAX bucket (16, 32 or 48), *kind to
    its kernel family (0 FP64, 1 double-double, else 2 limbs + fold) and
    *abs_shift to the scale of its sum of |terms|.  Needs no GPU.  Errors:
