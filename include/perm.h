@@ -32,8 +32,9 @@
  *     whose a-priori bound does not fit the widest exact mode (PERM_ERR_OVERFLOW).
  *   - Every kernel the library launches is its own hand-written CUDA (or CUDA
  *     C++ it generates and compiles with NVRTC for sm_103a).  There is no CPU
- *     fallback: without a usable CUDA device the compute calls return
- *     PERM_ERR_CUDA.
+ *     fallback: without a usable CUDA device every call that has a walk to do
+ *     returns PERM_ERR_CUDA (a matrix without a perfect matching, or an empty
+ *     sub-range, needs no walk and gives 0).
  */
 #ifndef PERM_H
 #define PERM_H
@@ -54,7 +55,8 @@ typedef enum {
     PERM_ERR_CUDA = 5,       /* a CUDA runtime/driver call failed (see last error)  */
     PERM_ERR_NVRTC = 6,      /* generating/compiling a per-matrix kernel failed     */
     PERM_ERR_NOMEM = 7,      /* host or device allocation failed                    */
-    PERM_ERR_TIMEOUT = 8,    /* a device-side wait ran out of iterations/time       */
+    PERM_ERR_TIMEOUT = 8,    /* timeout_ms passed: the device-side deadline of a    */
+                             /* walk, or a server request that waited too long      */
     PERM_ERR_BUSY = 9,       /* server refused a submit (admission budget full)     */
     PERM_ERR_NOT_READY = 10, /* perm_poll: the ticket has not finished yet          */
     PERM_ERR_CANCELLED = 11, /* server shut down before the ticket finished         */
