@@ -356,6 +356,15 @@ typedef struct {
                                  /*   of the generated walk (its rows folded in 32 bits */
                                  /*   as the generator folds them), in the ring of     */
                                  /*   exact_limbs limbs; 0 for FP64 inputs             */
+    /* A design study, not a scheme the kernels run: the FP64 operations per
+       step of four-state chains (column 1 kept out of x like column 0, so
+       every 4-step Gray quad flips only columns >= 2; a group of r rows costs
+       r + 3 into the four chains, a row of column 0 or 1 five operations, a
+       row of both seven; Lemma 2 weights as in the other models), on the
+       plan's column order and on an order searched for it by pairwise swaps.
+       0 for n < 3. */
+    double ops_per_step_four_state;
+    double ops_per_step_four_state_searched;
 } perm_inspect_t;
 
 perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts, perm_inspect_t *out);

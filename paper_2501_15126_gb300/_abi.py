@@ -74,7 +74,8 @@ class Inspect(ctypes.Structure):
                 ("group_size", c_i32 * 64), ("col_nnz", c_i32 * 64), ("reg_rows", c_i32), ("reg_cols", c_i32),
                 ("exact_words", c_i32), ("bound_log2", c_dbl), ("ops_per_step", c_dbl),
                 ("ops_per_step_paper", c_dbl), ("exact_limbs", c_i32), ("reserved0", c_i32),
-                ("ops_per_step_walk", c_dbl), ("ring_ops_per_step", c_dbl)]
+                ("ops_per_step_walk", c_dbl), ("ring_ops_per_step", c_dbl),
+                ("ops_per_step_four_state", c_dbl), ("ops_per_step_four_state_searched", c_dbl)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -873,6 +873,8 @@ perm_status_t perm_inspect(const perm_matrix_t *A, const perm_opts_t *opts_in, p
     out->ring_ops_per_step = m.is_int && out->exact_limbs ? ring_ops_per_step(m, L, out->exact_limbs, 1) : 0.0;
     out->ops_per_step = cost_per_step(L, false);
     out->ops_per_step_paper = cost_per_step(L, true);
+    out->ops_per_step_four_state = cost_per_step_four_state(m, L.col_order);
+    out->ops_per_step_four_state_searched = four_state_searched(m, L.col_order);
     return PERM_OK;
 }
 

@@ -347,6 +347,72 @@ static void search_order(const Matrix &m, int *cols, bool fp64, bool long_walk) 
     }
 }
 
+// Four-state chains (a design study; no kernel runs them): columns 0 and 1
+// are never applied to x, and four chains hold the products for the four
+// settings of the two columns, so every 4-step Gray quad flips only columns
+// >= 2.  A flip of column j >= 2 updates its nnz_j rows and rebuilds levels
+// j..2 of all four chains: a group of r rows is one product of r factors
+// multiplied into four chains (r + 3 operations); a row of column 0 or 1
+// whose next column is m joins level m as two variants (one add, four
+// multiplications), a row of both as four (three adds, four
+// multiplications).  Each quad's four products are combined and accumulated
+// (four operations).  Per step, with Lemma 2's flip rates.
+double cost_per_step_four_state(const Matrix &m, const int *cols) {
+    const int n = m.n;
+    if (n < 3) return 0.0;
+    int R[kNMax], d[kNMax], S1[kNMax + 1] = {}, S2[kNMax + 1] = {};
+    uint64_t seen = 0;
+    for (int p = 0; p < n; ++p) {
+        const uint64_t cm = m.colmask[cols[p]];
+        d[p] = __builtin_popcountll(cm);
+        R[p] = __builtin_popcountll(cm & ~seen);
+        seen |= cm;
+    }
+    const uint64_t c0 = m.colmask[cols[0]], c1 = m.colmask[cols[1]];
+    uint64_t one = c0 ^ c1, both = c0 & c1;
+    for (int p = 2; p < n - 1; ++p) {
+        const uint64_t cm = m.colmask[cols[p]];
+        S1[p] = __builtin_popcountll(cm & one);
+        S2[p] = __builtin_popcountll(cm & both);
+        one &= ~cm;
+        both &= ~cm;
+    }
+    const double steps = std::ldexp(1.0, n - 1) - 1.0;
+    double total = 0.0, rate = 0.0;
+    for (int j = n - 2; j >= 2; --j) {
+        const double w = std::ldexp(1.0, n - j - 2) / steps;
+        total += w * d[j];
+        rate += w;   // level j is rebuilt by a flip of any column >= j
+        total += rate * ((R[j] ? R[j] + 3.0 : 0.0) + 5.0 * S1[j] + 7.0 * S2[j]);
+    }
+    return total + 4.0 * std::ldexp(1.0, n - 3) / steps;
+}
+
+// The same pairwise-swap search as search_order, under the four-state model.
+double four_state_searched(const Matrix &m, const int *cols_in) {
+    const int n = m.n;
+    if (n < 3) return 0.0;
+    int cols[kNMax];
+    for (int p = 0; p < n; ++p) cols[p] = cols_in[p];
+    double best = cost_per_step_four_state(m, cols);
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        bool improved = false;
+        for (int i = 0; i + 1 < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                std::swap(cols[i], cols[j]);
+                const double c = cost_per_step_four_state(m, cols);
+                if (c < best - 1e-12) {
+                    best = c;
+                    improved = true;
+                } else {
+                    std::swap(cols[i], cols[j]);
+                }
+            }
+        if (!improved) break;
+    }
+    return best;
+}
+
 double walk_cost_per_step(const Layout &L, bool fp64) {
     if (!fp64) return cost_per_step(L, false);
     const double dual = cost_per_step_dual(L, true);

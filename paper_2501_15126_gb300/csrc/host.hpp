@@ -132,6 +132,10 @@ double walk_cost_per_step(const Layout &L, bool fp64);
 // group's rows whose row-sum product stays below 2^31 (generated kernels),
 // 2 = fixed slot quadruples (generic kernels, rows' absolute sums <= 127).
 double ring_ops_per_step(const Matrix &m, const Layout &L, int limbs, int fold);
+// Four-state chains (a design study): FP64 operations per step on a column
+// order, and after a pairwise-swap search for that model.
+double cost_per_step_four_state(const Matrix &m, const int *cols);
+double four_state_searched(const Matrix &m, const int *cols);
 
 // The fewest 32-bit limbs (2..6) of a ring that holds 2^(n-1) perm with sign
 // and margin, or 0.

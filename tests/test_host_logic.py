@@ -348,3 +348,46 @@ def test_register_budget_of_generated_kernels():
     assert blocks(synth.single_er(28, 0.3, 6, values="f64")) == 2                   # 2^27 steps
     assert blocks(synth.band_plus(48, 3, 2, seed=3, values="01")) == 2                # exact
     assert blocks(synth.band_plus(48, 3, 2, seed=3, values="f64")) == 1
+
+
+def _four_state_count(a, ins):
+    """Per-step operations of four-state chains by walking the Gray schedule
+    step by step: a flip of column j >= 2 updates its rows and rebuilds
+    levels j..2 of the four chains; columns 0 and 1 never touch x; every
+    fourth step closes a quad (four products combined and accumulated)."""
+    n = a.shape[0]
+    co = list(ins.col_order[:n])
+    nz = a[:, co] != 0
+    nnz = nz.sum(axis=0)
+    first = [int(np.argmax(nz[i])) for i in range(n)]
+    R = [first.count(m) for m in range(n)]
+    S1, S2 = [0] * n, [0] * n
+    for i in range(n):
+        if nz[i, 0] or nz[i, 1]:
+            nxt = next((p for p in range(2, n - 1) if nz[i, p]), None)
+            if nxt is not None:
+                (S2 if nz[i, 0] and nz[i, 1] else S1)[nxt] += 1
+    steps = (1 << (n - 1)) - 1
+    total = 0
+    for l in range(1, steps + 1):
+        j = (l & -l).bit_length() - 1
+        if j >= 2:
+            total += nnz[j] + sum((R[m] + 3 if R[m] else 0) + 5 * S1[m] + 7 * S2[m] for m in range(2, j + 1))
+        if l % 4 == 3:
+            total += 4
+    return total / steps
+
+
+def test_four_state_model_matches_a_step_by_step_count():
+    """The four-state study model (perm_inspect ops_per_step_four_state) equals
+    a direct count over the Gray schedule, and the order searched for it is
+    never worse than the plan's order."""
+    cases = [synth.single_er(12, 0.3, 1, values="f64"), synth.band_plus(14, 2, 1, seed=2, values="f64"),
+             synth.single_er(16, 0.2, 7, values="f64"), synth.ones(9).astype(np.float64)]
+    for a in cases:
+        ins = A.inspect(a)
+        want = _four_state_count(a, ins)
+        assert abs(ins.ops_per_step_four_state - want) < 1e-9 * want, (ins.ops_per_step_four_state, want)
+        assert ins.ops_per_step_four_state_searched <= ins.ops_per_step_four_state + 1e-12
+    big = A.inspect(synth.single_er(36, 0.15, 2, values="f64", shuffle_cols=True))
+    assert big.ops_per_step_four_state_searched < 0.8 * big.ops_per_step_walk
