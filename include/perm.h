@@ -428,7 +428,8 @@ const char *perm_status_string(perm_status_t s);
 const char *perm_last_error(void);
 /* 1 when a CUDA device is usable from this library, else 0 (never fails). */
 int32_t perm_device_available(void);
-/* Library version, e.g. "1.0.0". */
+/* Library version, "major.minor.patch" ("1.1.0": perm_inspect_t gained the
+   four-state study fields and perm_generic_image was added). */
 const char *perm_version(void);
 /* sizeof of the ABI structs, so bindings can check their layout:
    0 perm_matrix_t, 1 perm_opts_t, 2 perm_result_t, 3 perm_inspect_t,

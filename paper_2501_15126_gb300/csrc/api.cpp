@@ -964,7 +964,7 @@ int32_t perm_device_available(void) {
     return count > 0 ? 1 : 0;
 }
 
-const char *perm_version(void) { return "1.0.0"; }
+const char *perm_version(void) { return "1.1.0"; }
 
 int64_t perm_sizeof(int32_t which) {
     switch (which) {
